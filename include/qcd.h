@@ -1,0 +1,191 @@
+/* qcd.h - C-ABI of the GB300 Wilson-clover AMA library.
+ *
+ * The library solves the Dirac equation D psi = eta for O(a)-improved
+ * Wilson-clover quarks with a Schwarz-alternating-procedure (SAP)
+ * preconditioned flexible GCR solver, and forms the nucleon two-point
+ * function and its all-mode-averaging (AMA) estimate from point-source
+ * propagators (arXiv:1605.00564, Sec. 2).  Everything is computed by CUDA
+ * kernels on the caller's GPU; there is no CPU fallback.
+ *
+ * Conventions (all entry points):
+ *  - dims = {T, X, Y, Z}.  Site index s = ((t*Z + z)*Y + y)*X + x (x fastest).
+ *  - Canonical FP64 layouts, complex numbers as interleaved (re, im) doubles:
+ *      spinor     [rhs][site][spin 4][colour 3]
+ *      gauge      [site][mu 4][row 3][col 3], mu = 0 time, 1 x, 2 y, 3 z;
+ *                 U_mu(x) is the link from x to x + mu-hat
+ *      propagator the 12 spinors of one point source, rhs = 3*spin + colour
+ *  - The operator (kappa normalisation, chiral Euclidean gamma basis,
+ *    gamma_5 = diag(1,1,-1,-1), sigma_{mu nu} = (i/2)[g_mu, g_nu]):
+ *      D psi(x) = psi(x) - kappa sum_mu [(1 - g_mu) U_mu(x) psi(x+mu)
+ *                                      + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)]
+ *               + i kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x) psi(x)
+ *    F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^+)/8 from the four plaquette leaves
+ *    Q_{mu nu}; periodic in space, time_bc (+1 / -1) on hops across t = 0.
+ *  - Tolerances are relative: ||eta - D psi||_2 / ||eta||_2, evaluated in FP64.
+ *  - Ownership: the caller owns every buffer it passes; the library owns the
+ *    context and its internal copies and workspaces.  "device" pointers are
+ *    CUDA global memory of the context's device; "host" pointers are CPU
+ *    memory (pinned or pageable).  Work is ordered on the context's stream;
+ *    calls that return results to host memory synchronise that stream.
+ *  - Errors: every call returns a qcd_status; nothing throws across the ABI.
+ *    qcd_last_error() gives a message for the most recent failure of the
+ *    calling thread.  Argument errors are detected before any launch.
+ */
+#ifndef QCD_GB300_H
+#define QCD_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qcd_ctx qcd_ctx; /* opaque, library-owned */
+
+typedef enum {
+  QCD_OK = 0,
+  QCD_ERR_ARG = 1,            /* invalid argument (checked before any launch) */
+  QCD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  QCD_ERR_OOM = 3,            /* device allocation failed */
+  QCD_ERR_NOT_CONVERGED = 4,  /* solver hit max_outer; psi holds the best iterate */
+  QCD_ERR_BREAKDOWN = 5,      /* a Gram-Schmidt norm vanished */
+  QCD_ERR_NONFINITE = 6,      /* NaN or Inf in an input or a residual */
+  QCD_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+  QCD_ERR_STATE = 8           /* call out of order (e.g. solve before load_gauge) */
+} qcd_status;
+
+/* Precision of a computation.  QCD_PREC_F64 is the plain double-precision
+ * path; QCD_PREC_F32 stores and computes in single precision. */
+typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
+
+/* Solver parameters (Sec. 2.2: block size and n_cy are the SAP tunables;
+ * the GCR restart length and stopping rule are the outer solver's).
+ *   block       SAP block extents {T, X, Y, Z}; each must divide the lattice
+ *               and give an even number of blocks per direction
+ *               (checkerboard colouring of the blocks).  Block volume <= 1024.
+ *   ncy         SAP cycles per preconditioner application (paper: 5).
+ *   nmr         minimal-residual steps per block solve.
+ *   nkv         GCR Krylov vectors per restart cycle (<= 32).
+ *   max_outer   cap on GCR iterations (preconditioner applications) per RHS.
+ *   restart_drop  a restart cycle ends when the recursive residual fell by
+ *               this factor (0 = only at nkv); the true FP64 residual is then
+ *               recomputed.  Used with the mixed-precision policy.
+ *   precision   QCD_PREC_F32: FP64 outer vectors and true residuals, FP32 SAP
+ *               and Krylov basis (mixed precision, Sec. 2.2 last paragraph);
+ *               QCD_PREC_F64: everything in FP64.
+ *   rhs_tile    right-hand sides solved together (0 = library choice).
+ */
+typedef struct {
+  int block[4];
+  int ncy;
+  int nmr;
+  int nkv;
+  int max_outer;
+  double restart_drop;
+  int precision;
+  int rhs_tile;
+} qcd_solver_params;
+
+/* Per right-hand-side outcome of a solve. */
+typedef struct {
+  int status;                 /* QCD_OK or QCD_ERR_NOT_CONVERGED / ..._NONFINITE */
+  int outer_iters;            /* GCR iterations (preconditioner applications) */
+  int restarts;               /* true-residual recomputations */
+  double true_rel_residual;   /* FP64 ||eta - D psi|| / ||eta|| at exit */
+} qcd_rhs_stats;
+
+/* Message for a status code (static string). */
+const char* qcd_status_string(qcd_status s);
+/* Message of the last failure in this thread (static per-thread buffer). */
+const char* qcd_last_error(void);
+
+/* Create a context for a lattice dims = {T, X, Y, Z} on the current CUDA
+ * device.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * Each extent must be >= 2; T*X*Y*Z < 2^31. */
+qcd_status qcd_create(qcd_ctx** out, const int dims[4], void* cuda_stream);
+void qcd_destroy(qcd_ctx* ctx);
+
+/* Load the gauge field and the operator's couplings (Sec. 2.2, the Dirac
+ * equation D psi = eta for O(a)-improved Wilson quarks).  U is canonical
+ * FP64, on the device when U_on_device != 0, else host.  The clover term is
+ * built on the device from the plaquette leaves.  time_bc is +1 or -1. */
+qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int U_on_device, double csw, double kappa,
+                          int time_bc);
+
+/* Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
+ * restart_drop 1e-5, precision F32, rhs_tile 0. */
+void qcd_default_params(qcd_solver_params* p);
+qcd_status qcd_set_params(qcd_ctx* ctx, const qcd_solver_params* p);
+
+/* out = D in (dagger = 0) or D^+ in (dagger = 1) for nrhs canonical spinors
+ * on the device, computed in the given precision (inputs are rounded to it;
+ * the output is written back in FP64).  in and out must not overlap. */
+qcd_status qcd_apply_dirac(qcd_ctx* ctx, const double* in, double* out, int nrhs, int dagger, int precision);
+
+/* psi = M_SAP eta: n_cy SAP cycles from psi = 0 with nmr MR steps per block
+ * solve (Sec. 2.2, M_SAP = K sum_{nu<n_cy} (1 - D K)^nu, inexact blocks).
+ * Device canonical spinors, precision F64 or F32. */
+qcd_status qcd_apply_sap(qcd_ctx* ctx, const double* eta, double* psi, int nrhs, int precision);
+
+/* Solve D psi = eta for nrhs device canonical spinors with SAP-preconditioned
+ * flexible GCR (Sec. 2.2: D M_SAP phi = eta, psi = M_SAP phi).  psi holds the
+ * initial guess on entry (zeros for none).  rel_tol is a host array of nrhs
+ * tolerances.  stats (host, nrhs entries) may be NULL.  Returns QCD_OK when
+ * every RHS converged, else QCD_ERR_NOT_CONVERGED (psi = best iterates). */
+qcd_status qcd_solve(qcd_ctx* ctx, const double* eta, double* psi, int nrhs, const double* rel_tol,
+                     qcd_rhs_stats* stats);
+
+/* Nucleon two-point function (eq. Nop, N = eps^{abc} (u^a^T C g5 d^b) u^c,
+ * C = g0 g2, u = d) from one point-source propagator prop (device,
+ * canonical, 12 spinors rhs = 3*spin + colour) with source src = {t,x,y,z}:
+ *   corr[p][t][re/im], p = 0: tr[P+ G], p = 1: tr[P- G], P+- = (1 +- g0)/2,
+ *   G(t) = sum_{x-vec} <N(x,t) N-bar(src)>, t relative to the source time;
+ *   a sink time that wraps past T is multiplied by time_bc^3.
+ * corr is host memory of 2*T*2 doubles.  precision selects FP64 or FP32
+ * arithmetic. */
+qcd_status qcd_nucleon_2pt(qcd_ctx* ctx, const double* prop, const int src[4], double* corr, int precision);
+
+/* AMA estimate of the nucleon two-point function (eqs. caa1, caa2):
+ *   O_AMA = (1/N_org) sum_f [O^f - O_appx^f] + (1/N_G) sum_g O_appx^g.
+ * For each of n_src source positions src[4*i..] the 12 spin-colour point
+ * sources are solved to sloppy_tol; the first n_exact positions are also
+ * solved to exact_tol (the bias correction, N_org = n_exact).  Positions must
+ * be multiples of the SAP block extents so that the translations map the
+ * block decomposition onto itself (Sec. 2.2, end).
+ *   corr_ama  host [2][T][2]          the AMA estimate
+ *   corr_all  host [n_src + n_exact][2][T][2] or NULL: sloppy correlators
+ *             of every source, then exact correlators of the first n_exact
+ *   stats     host [(n_src + n_exact) * 12] or NULL, same order. */
+qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_exact, double sloppy_tol,
+                               double exact_tol, double* corr_ama, double* corr_all, qcd_rhs_stats* stats);
+
+/* The site-diagonal part A(x) = 1 + i kappa c_sw sum sigma F of the operator
+ * as [site][chirality 2][6][6] complex FP64 (device), chirality block 0 acting
+ * on spins 0,1 and block 1 on spins 2,3, index 3*(spin & 1) + colour. */
+qcd_status qcd_get_clover(qcd_ctx* ctx, double* out);
+
+/* Kernel timing (no counterpart in the paper; measurement support).  While
+ * enabled, every kernel launch of the library on the context's stream is
+ * bracketed by CUDA events.  qcd_profile_read synchronises the stream and
+ * returns, per kernel family, the launches, their summed device time and
+ * the algorithmic bytes they had to move (each input word read once, each
+ * output word written once), then clears the records.
+ * Families: "dslash_f64", "dslash_f32", "sap_f64", "sap_f32", "blas",
+ * "layout", "contract". */
+typedef struct {
+  char name[24];
+  int launches;
+  double ms;
+  double bytes;
+  double flops;
+} qcd_kernel_time;
+
+qcd_status qcd_profile_enable(qcd_ctx* ctx, int on);
+/* out: host array of max entries; *n receives the number of families filled. */
+qcd_status qcd_profile_read(qcd_ctx* ctx, qcd_kernel_time* out, int max, int* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCD_GB300_H */

@@ -1,0 +1,322 @@
+// Vector operations of the GCR solver on internal spinor layouts:
+// norms and inner products (two-stage, fixed-order reductions: the same
+// inputs always give the same bits), complex axpy with per-RHS
+// coefficients read from device memory, scaling and precision conversion.
+//
+// A spinor of either precision is viewed as 6 V "pairs" of complex numbers:
+// pair (k, s) holds components 2k and 2k+1 of site s.  FP32 stores a pair as
+// one float4 at k*V + s; FP64 as two double2 at 2k*V + s and (2k+1)*V + s.
+#include "qcd_internal.cuh"
+
+namespace {
+
+constexpr int RED_TPB = 256;
+
+struct PD {  // FP64 pair access
+  using R = double;
+  static constexpr size_t bytes = 192;
+  static __device__ inline void ld(const char* b, int V, int k, int s, Cplx<double>& a, Cplx<double>& c) {
+    const double2* p = (const double2*)b;
+    double2 x = p[(size_t)(2 * k) * V + s], y = p[(size_t)(2 * k + 1) * V + s];
+    a = cmk(x.x, x.y);
+    c = cmk(y.x, y.y);
+  }
+  static __device__ inline void st(char* b, int V, int k, int s, Cplx<double> a, Cplx<double> c) {
+    double2* p = (double2*)b;
+    p[(size_t)(2 * k) * V + s] = make_double2(a.re, a.im);
+    p[(size_t)(2 * k + 1) * V + s] = make_double2(c.re, c.im);
+  }
+};
+struct PF {  // FP32 pair access
+  using R = float;
+  static constexpr size_t bytes = 96;
+  static __device__ inline void ld(const char* b, int V, int k, int s, Cplx<float>& a, Cplx<float>& c) {
+    float4 v = ((const float4*)b)[(size_t)k * V + s];
+    a = cmk(v.x, v.y);
+    c = cmk(v.z, v.w);
+  }
+  static __device__ inline void st(char* b, int V, int k, int s, Cplx<float> a, Cplx<float> c) {
+    ((float4*)b)[(size_t)k * V + s] = make_float4(a.re, a.im, c.re, c.im);
+  }
+};
+
+// arithmetic type of a mixed product: FP32 only when both sides are FP32
+template <typename X, typename Y>
+struct Acc { using R = double; };
+template <>
+struct Acc<PF, PF> { using R = float; };
+
+__device__ inline double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// block-wide sum in a fixed order; result valid in thread 0
+__device__ inline double2 block_sum(double2 v) {
+  __shared__ double2 sh[32];
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double2 t = make_double2(0, 0);
+  if (w == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    t = l < nw ? sh[l] : make_double2(0, 0);
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// OP 0: sum |x|^2 ; OP 1: sum conj(x) y
+template <typename X, typename Y, int OP>
+__global__ void __launch_bounds__(RED_TPB) k_reduce(const char* __restrict__ x, const char* __restrict__ y, int V,
+                                                    double2* __restrict__ part, const int* mask) {
+  const int rhs = blockIdx.y;
+  double2 acc = make_double2(0, 0);
+  if (!mask || mask[rhs]) {
+    using R = typename Acc<X, Y>::R;
+    const char* xb = x + (size_t)rhs * X::bytes * V;
+    const char* yb = OP ? y + (size_t)rhs * Y::bytes * V : nullptr;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+      R sr = 0, si = 0;
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        Cplx<typename X::R> a, b;
+        X::ld(xb, V, k, s, a, b);
+        if (OP == 0) {
+          sr += (R)a.re * (R)a.re + (R)a.im * (R)a.im + (R)b.re * (R)b.re + (R)b.im * (R)b.im;
+        } else {
+          Cplx<typename Y::R> c, d;
+          Y::ld(yb, V, k, s, c, d);
+          sr += (R)a.re * (R)c.re + (R)a.im * (R)c.im + (R)b.re * (R)d.re + (R)b.im * (R)d.im;
+          si += (R)a.re * (R)c.im - (R)a.im * (R)c.re + (R)b.re * (R)d.im - (R)b.im * (R)d.re;
+        }
+      }
+      acc.x += (double)sr;
+      acc.y += (double)si;
+    }
+  }
+  double2 t = block_sum(acc);
+  if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = t;
+}
+
+// sum the G partials of each rhs in a fixed order
+__global__ void __launch_bounds__(RED_TPB) k_reduce_final(const double2* __restrict__ part, int G, double2* out,
+                                                          int cplx, const int* mask) {
+  const int rhs = blockIdx.x;
+  if (mask && !mask[rhs]) return;
+  double2 acc = make_double2(0, 0);
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    double2 v = part[(size_t)rhs * G + i];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  double2 t = block_sum(acc);
+  if (threadIdx.x == 0) {
+    if (cplx)
+      out[rhs] = t;
+    else
+      ((double*)out)[rhs] = t.x;
+  }
+}
+
+int red_grid(const qcd_ctx* c) {
+  int g = (c->g.V + RED_TPB - 1) / RED_TPB;
+  return g < 4 * 152 ? g : 4 * 152;
+}
+
+template <typename X, typename Y, int OP>
+qcd_status reduce(qcd_ctx* c, const void* x, const void* y, int nrhs, void* out, const int* mask) {
+  int G = red_grid(c);
+  QCD_TRY(devbuf_ensure(c->red, (size_t)G * nrhs * sizeof(double2)));
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nrhs * (X::bytes + (OP ? Y::bytes : 0)), (double)c->g.V * nrhs * 96);
+  k_reduce<X, Y, OP><<<dim3(G, nrhs), RED_TPB, 0, c->stream>>>((const char*)x, (const char*)y, c->g.V,
+                                                                (double2*)c->red.p, mask);
+  k_reduce_final<<<nrhs, RED_TPB, 0, c->stream>>>((const double2*)c->red.p, G, (double2*)out, OP, mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+// y_r += sign * sum_j coef[j*nrhs + r] * x_{j,r}
+template <typename Y, typename X>
+__global__ void k_multi_caxpy(char* __restrict__ y, const char* __restrict__ xbase, int nx, size_t xstride,
+                              const double2* __restrict__ coef, double sign, int V, int nrhs, const int* mask) {
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  using R = typename Y::R;
+  char* yb = y + (size_t)rhs * Y::bytes * V;
+#pragma unroll 1
+  for (int k = 0; k < 6; k++) {
+    Cplx<R> a, b;
+    Y::ld(yb, V, k, s, a, b);
+    Cplx<double> ad = cmk((double)a.re, (double)a.im), bd = cmk((double)b.re, (double)b.im);
+    for (int j = 0; j < nx; j++) {
+      double2 cf = coef[(size_t)j * nrhs + rhs];
+      Cplx<double> w = cmk(sign * cf.x, sign * cf.y);
+      Cplx<typename X::R> u, v;
+      X::ld(xbase + j * xstride + (size_t)rhs * X::bytes * V, V, k, s, u, v);
+      ad = ad + w * cmk((double)u.re, (double)u.im);
+      bd = bd + w * cmk((double)v.re, (double)v.im);
+    }
+    Y::st(yb, V, k, s, cmk((R)ad.re, (R)ad.im), cmk((R)bd.re, (R)bd.im));
+  }
+}
+
+// FP32 specialisation: coefficients applied in FP32
+template <>
+__global__ void k_multi_caxpy<PF, PF>(char* __restrict__ y, const char* __restrict__ xbase, int nx, size_t xstride,
+                                      const double2* __restrict__ coef, double sign, int V, int nrhs,
+                                      const int* mask) {
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  float4* yb = (float4*)(y + (size_t)rhs * PF::bytes * V);
+#pragma unroll 1
+  for (int k = 0; k < 6; k++) {
+    float4 a = yb[(size_t)k * V + s];
+    for (int j = 0; j < nx; j++) {
+      double2 cf = coef[(size_t)j * nrhs + rhs];
+      float wr = (float)(sign * cf.x), wi = (float)(sign * cf.y);
+      float4 u = ((const float4*)(xbase + j * xstride + (size_t)rhs * PF::bytes * V))[(size_t)k * V + s];
+      a.x += wr * u.x - wi * u.y;
+      a.y += wr * u.y + wi * u.x;
+      a.z += wr * u.z - wi * u.w;
+      a.w += wr * u.w + wi * u.z;
+    }
+    yb[(size_t)k * V + s] = a;
+  }
+}
+
+template <typename X>
+__global__ void k_scale(char* __restrict__ x, const double* __restrict__ sc, int V, int nrhs, const int* mask) {
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  using R = typename X::R;
+  R f = (R)sc[rhs];
+  char* xb = x + (size_t)rhs * X::bytes * V;
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    Cplx<R> a, b;
+    X::ld(xb, V, k, s, a, b);
+    X::st(xb, V, k, s, f * a, f * b);
+  }
+}
+
+// out = x - y (same precision)
+template <typename X>
+__global__ void k_xmy(const char* __restrict__ x, const char* __restrict__ y, char* __restrict__ out, int V, int nrhs,
+                      const int* mask) {
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  size_t off = (size_t)rhs * X::bytes * V;
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    Cplx<typename X::R> a, b, c, d;
+    X::ld(x + off, V, k, s, a, b);
+    X::ld(y + off, V, k, s, c, d);
+    X::st(out + off, V, k, s, a - c, b - d);
+  }
+}
+
+template <typename I, typename O>
+__global__ void k_convert(const char* __restrict__ in, char* __restrict__ out, int V, int nrhs, const int* mask) {
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  using RO = typename O::R;
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    Cplx<typename I::R> a, b;
+    I::ld(in + (size_t)rhs * I::bytes * V, V, k, s, a, b);
+    O::st(out + (size_t)rhs * O::bytes * V, V, k, s, cmk((RO)a.re, (RO)a.im), cmk((RO)b.re, (RO)b.im));
+  }
+}
+
+inline dim3 grid2(const qcd_ctx* c, int nrhs) { return dim3((c->g.V + 255) / 256, nrhs); }
+
+}  // namespace
+
+qcd_status blas_norm2(qcd_ctx* c, const void* x, int prec, int nrhs, double* out_dev, const int* mask) {
+  if (prec == QCD_PREC_F64) return reduce<PD, PD, 0>(c, x, nullptr, nrhs, out_dev, mask);
+  return reduce<PF, PF, 0>(c, x, nullptr, nrhs, out_dev, mask);
+}
+
+qcd_status blas_dot(qcd_ctx* c, const void* x, int px, const void* y, int py, int nrhs, double* out_dev,
+                    const int* mask) {
+  if (px == QCD_PREC_F64 && py == QCD_PREC_F64) return reduce<PD, PD, 1>(c, x, y, nrhs, out_dev, mask);
+  if (px == QCD_PREC_F32 && py == QCD_PREC_F64) return reduce<PF, PD, 1>(c, x, y, nrhs, out_dev, mask);
+  if (px == QCD_PREC_F64 && py == QCD_PREC_F32) return reduce<PD, PF, 1>(c, x, y, nrhs, out_dev, mask);
+  return reduce<PF, PF, 1>(c, x, y, nrhs, out_dev, mask);
+}
+
+qcd_status blas_multi_caxpy(qcd_ctx* c, void* y, int py, const void* xbase, int px, int nx, size_t xstride,
+                            const double* coef_dev, double sign, int nrhs, const int* mask) {
+  if (nx <= 0) return QCD_OK;
+  dim3 g = grid2(c, nrhs);
+  const double by = py == QCD_PREC_F64 ? 192 : 96, bx = px == QCD_PREC_F64 ? 192 : 96;
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nrhs * (2 * by + nx * bx), (double)c->g.V * nrhs * nx * 96);
+  if (py == QCD_PREC_F64 && px == QCD_PREC_F64)
+    k_multi_caxpy<PD, PD><<<g, 256, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride,
+                                                    (const double2*)coef_dev, sign, c->g.V, nrhs, mask);
+  else if (py == QCD_PREC_F64 && px == QCD_PREC_F32)
+    k_multi_caxpy<PD, PF><<<g, 256, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride,
+                                                    (const double2*)coef_dev, sign, c->g.V, nrhs, mask);
+  else if (py == QCD_PREC_F32 && px == QCD_PREC_F32)
+    k_multi_caxpy<PF, PF><<<g, 256, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride,
+                                                    (const double2*)coef_dev, sign, c->g.V, nrhs, mask);
+  else {
+    qcd_set_error("multi_caxpy: unsupported precision pair");
+    return QCD_ERR_ARG;
+  }
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+qcd_status blas_scale(qcd_ctx* c, void* x, int px, const double* sc_dev, int nrhs, const int* mask) {
+  dim3 g = grid2(c, nrhs);
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nrhs * 2 * (px == QCD_PREC_F64 ? 192 : 96), (double)c->g.V * nrhs * 24);
+  if (px == QCD_PREC_F64)
+    k_scale<PD><<<g, 256, 0, c->stream>>>((char*)x, sc_dev, c->g.V, nrhs, mask);
+  else
+    k_scale<PF><<<g, 256, 0, c->stream>>>((char*)x, sc_dev, c->g.V, nrhs, mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+qcd_status blas_xmy(qcd_ctx* c, const void* x, const void* y, void* out, int prec, int nrhs, const int* mask) {
+  dim3 g = grid2(c, nrhs);
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nrhs * 3 * (prec == QCD_PREC_F64 ? 192 : 96), (double)c->g.V * nrhs * 24);
+  if (prec == QCD_PREC_F64)
+    k_xmy<PD><<<g, 256, 0, c->stream>>>((const char*)x, (const char*)y, (char*)out, c->g.V, nrhs, mask);
+  else
+    k_xmy<PF><<<g, 256, 0, c->stream>>>((const char*)x, (const char*)y, (char*)out, c->g.V, nrhs, mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+qcd_status blas_convert(qcd_ctx* c, const void* in, int pin, void* out, int pout, int nrhs, const int* mask) {
+  dim3 g = grid2(c, nrhs);
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nrhs * ((pin == QCD_PREC_F64 ? 192 : 96) + (pout == QCD_PREC_F64 ? 192 : 96)), 0.0);
+  if (pin == QCD_PREC_F64 && pout == QCD_PREC_F32)
+    k_convert<PD, PF><<<g, 256, 0, c->stream>>>((const char*)in, (char*)out, c->g.V, nrhs, mask);
+  else if (pin == QCD_PREC_F32 && pout == QCD_PREC_F64)
+    k_convert<PF, PD><<<g, 256, 0, c->stream>>>((const char*)in, (char*)out, c->g.V, nrhs, mask);
+  else if (pin == QCD_PREC_F64 && pout == QCD_PREC_F64)
+    k_convert<PD, PD><<<g, 256, 0, c->stream>>>((const char*)in, (char*)out, c->g.V, nrhs, mask);
+  else
+    k_convert<PF, PF><<<g, 256, 0, c->stream>>>((const char*)in, (char*)out, c->g.V, nrhs, mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}

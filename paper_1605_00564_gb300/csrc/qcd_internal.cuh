@@ -1,0 +1,388 @@
+// Internal types, field layouts and device helpers of the Wilson-clover
+// library.  Nothing here is part of the public C-ABI (include/qcd.h).
+//
+// Site order everywhere is lexicographic, s = ((t*LZ + z)*LY + y)*LX + x.
+// Internal layouts are structure-of-arrays over sites so that consecutive
+// threads (consecutive sites) read consecutive 16-byte words:
+//
+//   spinor FP64   double2 [rhs][12][V]   component c = 3*spin + colour
+//   spinor FP32   float4  [rhs][6][V]    float4 k = components 2k, 2k+1
+//   gauge  FP64   double2 [4][9][V]      U_mu(x)[row][col], full matrix
+//   gauge  FP32   float4  [4][3][V]      rows 0 and 1; row 2 = conj(r0 x r1)
+//   clover FP64   double2 [36][V]        two packed 6x6 Hermitian chiral blocks
+//   clover FP32   float4  [18][V]        same 72 reals in groups of four
+//
+// A packed Hermitian 6x6 block holds its 6 real diagonal entries followed by
+// the 15 complex entries below the diagonal in row order
+// (1,0),(2,0),(2,1),(3,0),...,(5,4).  Block 0 acts on spins 0,1 (gamma_5 =
+// +1), block 1 on spins 2,3; the block index within a chirality is
+// 3*(spin & 1) + colour.  The stored matrix includes the unit diagonal of
+// the operator: A(x) = 1 + i kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "../../include/qcd.h"
+
+#define QCD_CUDA_OK(call)                                                    \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      qcd_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,              \
+                    cudaGetErrorString(e_));                                 \
+      return QCD_ERR_CUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+#define QCD_TRY(call)                                                        \
+  do {                                                                       \
+    qcd_status s_ = (call);                                                  \
+    if (s_ != QCD_OK) return s_;                                             \
+  } while (0)
+
+void qcd_set_error(const char* fmt, ...);
+
+// --------------------------------------------------------------------------
+// Geometry
+// --------------------------------------------------------------------------
+struct Geom {
+  int L[4];        // extents indexed by direction mu: 0 = t, 1 = x, 2 = y, 3 = z
+  int V;           // sites
+  int stride[4];   // site-index stride of a unit step in direction mu
+  int bc_t;        // +1 periodic, -1 antiperiodic in time
+};
+
+__host__ __device__ inline void site_coords(const Geom& g, int s, int c[4]) {
+  c[1] = s % g.L[1];
+  int r = s / g.L[1];
+  c[2] = r % g.L[2];
+  r /= g.L[2];
+  c[3] = r % g.L[3];
+  c[0] = r / g.L[3];
+}
+
+// neighbour of site s (coordinate c) one step forward / backward in mu
+__host__ __device__ inline int site_fwd(const Geom& g, int s, const int c[4], int mu) {
+  return (c[mu] == g.L[mu] - 1) ? s - (g.L[mu] - 1) * g.stride[mu] : s + g.stride[mu];
+}
+__host__ __device__ inline int site_bwd(const Geom& g, int s, const int c[4], int mu) {
+  return (c[mu] == 0) ? s + (g.L[mu] - 1) * g.stride[mu] : s - g.stride[mu];
+}
+
+// --------------------------------------------------------------------------
+// Complex arithmetic on (re, im) pairs of a real type R
+// --------------------------------------------------------------------------
+template <typename R>
+struct Cplx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ inline Cplx<R> cmk(R a, R b) { Cplx<R> z; z.re = a; z.im = b; return z; }
+template <typename R>
+__host__ __device__ inline Cplx<R> operator+(Cplx<R> a, Cplx<R> b) { return cmk(a.re + b.re, a.im + b.im); }
+template <typename R>
+__host__ __device__ inline Cplx<R> operator-(Cplx<R> a, Cplx<R> b) { return cmk(a.re - b.re, a.im - b.im); }
+template <typename R>
+__host__ __device__ inline Cplx<R> operator-(Cplx<R> a) { return cmk(-a.re, -a.im); }
+template <typename R>
+__host__ __device__ inline Cplx<R> operator*(Cplx<R> a, Cplx<R> b) {
+  return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ inline Cplx<R> operator*(R a, Cplx<R> b) { return cmk(a * b.re, a * b.im); }
+template <typename R>
+__host__ __device__ inline Cplx<R> conj(Cplx<R> a) { return cmk(a.re, -a.im); }
+// conj(a) * b
+template <typename R>
+__host__ __device__ inline Cplx<R> cdot(Cplx<R> a, Cplx<R> b) {
+  return cmk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+// i * a, -i * a
+template <typename R>
+__host__ __device__ inline Cplx<R> mul_i(Cplx<R> a) { return cmk(-a.im, a.re); }
+template <typename R>
+__host__ __device__ inline Cplx<R> mul_mi(Cplx<R> a) { return cmk(a.im, -a.re); }
+
+template <typename R>
+struct Spinor {
+  Cplx<R> c[12];   // 3*spin + colour
+};
+template <typename R>
+struct HalfSpinor {
+  Cplx<R> c[6];    // 3*s + colour, s = 0, 1
+};
+template <typename R>
+struct SU3 {
+  Cplx<R> m[3][3];
+};
+
+// --------------------------------------------------------------------------
+// Spin projection in the chiral basis.  gamma_mu = [[0, e_mu], [e_mu^+, 0]]
+// with e_0 = -1, e_k = -i sigma_k, so (1 -+ gamma_mu) psi = [h; -+ e_mu^+ h]
+// with h = psi_up -+ e_mu psi_dn.  SIGN = -1 builds the (1 - gamma_mu)
+// projection, SIGN = +1 the (1 + gamma_mu) projection.
+// --------------------------------------------------------------------------
+// w = e_mu v for a 2-spinor (per colour), e_0 = -1, e_k = -i sigma_k
+template <int MU, typename R>
+__host__ __device__ inline void e_mul(const Cplx<R> v0, const Cplx<R> v1, Cplx<R>& w0, Cplx<R>& w1) {
+  if (MU == 0) { w0 = -v0; w1 = -v1; }
+  if (MU == 1) { w0 = mul_mi(v1); w1 = mul_mi(v0); }          // -i sigma_1
+  if (MU == 2) { w0 = -v1; w1 = v0; }                          // -i sigma_2 = [[0,-1],[1,0]]
+  if (MU == 3) { w0 = mul_mi(v0); w1 = mul_i(v1); }            // -i sigma_3
+}
+// w = e_mu^+ v, e_0^+ = -1, e_k^+ = i sigma_k
+template <int MU, typename R>
+__host__ __device__ inline void edag_mul(const Cplx<R> v0, const Cplx<R> v1, Cplx<R>& w0, Cplx<R>& w1) {
+  if (MU == 0) { w0 = -v0; w1 = -v1; }
+  if (MU == 1) { w0 = mul_i(v1); w1 = mul_i(v0); }            // i sigma_1
+  if (MU == 2) { w0 = v1; w1 = -v0; }                          // i sigma_2 = [[0,1],[-1,0]]
+  if (MU == 3) { w0 = mul_i(v0); w1 = mul_mi(v1); }            // i sigma_3
+}
+
+template <int MU, int SIGN, typename R>
+__host__ __device__ inline HalfSpinor<R> project(const Spinor<R>& p) {
+  HalfSpinor<R> h;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Cplx<R> w0, w1;
+    e_mul<MU>(p.c[6 + a], p.c[9 + a], w0, w1);
+    if (SIGN < 0) { h.c[a] = p.c[a] - w0; h.c[3 + a] = p.c[3 + a] - w1; }
+    else          { h.c[a] = p.c[a] + w0; h.c[3 + a] = p.c[3 + a] + w1; }
+  }
+  return h;
+}
+
+// out += scale * (1 SIGN gamma_mu)-reconstruction of h
+template <int MU, int SIGN, typename R>
+__host__ __device__ inline void accum_recon(Spinor<R>& out, const HalfSpinor<R>& h, R scale) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Cplx<R> w0, w1;
+    edag_mul<MU>(h.c[a], h.c[3 + a], w0, w1);
+    out.c[a] = out.c[a] + scale * h.c[a];
+    out.c[3 + a] = out.c[3 + a] + scale * h.c[3 + a];
+    if (SIGN < 0) { out.c[6 + a] = out.c[6 + a] - scale * w0; out.c[9 + a] = out.c[9 + a] - scale * w1; }
+    else          { out.c[6 + a] = out.c[6 + a] + scale * w0; out.c[9 + a] = out.c[9 + a] + scale * w1; }
+  }
+}
+
+template <typename R>
+__host__ __device__ inline HalfSpinor<R> su3_mul(const SU3<R>& U, const HalfSpinor<R>& h) {
+  HalfSpinor<R> o;
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      o.c[3 * s + a] = U.m[a][0] * h.c[3 * s] + U.m[a][1] * h.c[3 * s + 1] + U.m[a][2] * h.c[3 * s + 2];
+  return o;
+}
+template <typename R>
+__host__ __device__ inline HalfSpinor<R> su3_dag_mul(const SU3<R>& U, const HalfSpinor<R>& h) {
+  HalfSpinor<R> o;
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      o.c[3 * s + a] = cdot(U.m[0][a], h.c[3 * s]) + cdot(U.m[1][a], h.c[3 * s + 1]) + cdot(U.m[2][a], h.c[3 * s + 2]);
+  return o;
+}
+
+// --------------------------------------------------------------------------
+// Field access by precision.  Each precision has a storage struct with
+// load/store for spinors, links and the clover term.
+// --------------------------------------------------------------------------
+struct FieldsD {   // FP64
+  using R = double;
+  static __device__ inline Spinor<double> load_spinor(const void* base, int V, int s) {
+    const double2* p = (const double2*)base;
+    Spinor<double> o;
+#pragma unroll
+    for (int c = 0; c < 12; c++) { double2 v = __ldg(p + (size_t)c * V + s); o.c[c] = cmk(v.x, v.y); }
+    return o;
+  }
+  static __device__ inline void store_spinor(void* base, int V, int s, const Spinor<double>& o) {
+    double2* p = (double2*)base;
+#pragma unroll
+    for (int c = 0; c < 12; c++) p[(size_t)c * V + s] = make_double2(o.c[c].re, o.c[c].im);
+  }
+  static __device__ inline SU3<double> load_link(const void* base, int V, int mu, int s) {
+    const double2* p = (const double2*)base + (size_t)mu * 9 * V;
+    SU3<double> U;
+#pragma unroll
+    for (int k = 0; k < 9; k++) { double2 v = __ldg(p + (size_t)k * V + s); U.m[k / 3][k % 3] = cmk(v.x, v.y); }
+    return U;
+  }
+  // the 36 reals of chirality block b (0 or 1)
+  static __device__ inline void load_clover_block(const void* base, int V, int s, int b, double (&cl)[36]) {
+    const double2* p = (const double2*)base + (size_t)18 * b * V;
+#pragma unroll
+    for (int k = 0; k < 18; k++) { double2 v = __ldg(p + (size_t)k * V + s); cl[2 * k] = v.x; cl[2 * k + 1] = v.y; }
+  }
+  static constexpr size_t spinor_bytes = 192, link_bytes = 144, clover_bytes = 576;
+};
+
+struct FieldsF {   // FP32
+  using R = float;
+  static __device__ inline Spinor<float> load_spinor(const void* base, int V, int s) {
+    const float4* p = (const float4*)base;
+    Spinor<float> o;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      float4 v = __ldg(p + (size_t)k * V + s);
+      o.c[2 * k] = cmk(v.x, v.y);
+      o.c[2 * k + 1] = cmk(v.z, v.w);
+    }
+    return o;
+  }
+  static __device__ inline void store_spinor(void* base, int V, int s, const Spinor<float>& o) {
+    float4* p = (float4*)base;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+      p[(size_t)k * V + s] = make_float4(o.c[2 * k].re, o.c[2 * k].im, o.c[2 * k + 1].re, o.c[2 * k + 1].im);
+  }
+  static __device__ inline SU3<float> load_link(const void* base, int V, int mu, int s) {
+    const float4* p = (const float4*)base + (size_t)mu * 3 * V;
+    float4 a = __ldg(p + s), b = __ldg(p + (size_t)V + s), c = __ldg(p + 2 * (size_t)V + s);
+    SU3<float> U;
+    U.m[0][0] = cmk(a.x, a.y); U.m[0][1] = cmk(a.z, a.w); U.m[0][2] = cmk(b.x, b.y);
+    U.m[1][0] = cmk(b.z, b.w); U.m[1][1] = cmk(c.x, c.y); U.m[1][2] = cmk(c.z, c.w);
+    // row 2 = conj(row0 x row1)
+    U.m[2][0] = conj(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
+    U.m[2][1] = conj(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
+    U.m[2][2] = conj(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
+    return U;
+  }
+  static __device__ inline void load_clover_block(const void* base, int V, int s, int b, float (&cl)[36]) {
+    const float4* p = (const float4*)base + (size_t)9 * b * V;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      float4 v = __ldg(p + (size_t)k * V + s);
+      cl[4 * k] = v.x; cl[4 * k + 1] = v.y; cl[4 * k + 2] = v.z; cl[4 * k + 3] = v.w;
+    }
+  }
+  static constexpr size_t spinor_bytes = 96, link_bytes = 48, clover_bytes = 288;
+};
+
+// Apply one packed Hermitian 6x6 block (36 reals starting at cl[k0]) to v.
+template <typename R>
+__host__ __device__ inline void clover_block_apply(const R* cl, int k0, const Cplx<R>* v, Cplx<R>* out) {
+#pragma unroll
+  for (int i = 0; i < 6; i++) out[i] = cl[k0 + i] * v[i];
+  int k = k0 + 6;
+#pragma unroll
+  for (int i = 1; i < 6; i++) {
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      Cplx<R> h = cmk(cl[k], cl[k + 1]);
+      k += 2;
+      out[i] = out[i] + h * v[j];
+      out[j] = out[j] + cdot(h, v[i]);
+    }
+  }
+}
+
+// A(x) psi(x): the site-diagonal part of the operator (unit + clover term),
+// one chirality block at a time
+template <typename F>
+__device__ inline Spinor<typename F::R> clover_apply(const void* clv, int V, int s, const Spinor<typename F::R>& p) {
+  Spinor<typename F::R> o;
+#pragma unroll
+  for (int b = 0; b < 2; b++) {
+    typename F::R cl[36];
+    F::load_clover_block(clv, V, s, b, cl);
+    clover_block_apply(cl, 0, &p.c[6 * b], &o.c[6 * b]);
+  }
+  return o;
+}
+
+// --------------------------------------------------------------------------
+// The context
+// --------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+qcd_status devbuf_ensure(DevBuf& b, size_t bytes);
+void devbuf_free(DevBuf& b);
+
+// kernel families of the timing records (qcd_profile_read)
+enum ProfFam { FAM_DSLASH_D, FAM_DSLASH_F, FAM_SAP_D, FAM_SAP_F, FAM_BLAS, FAM_LAYOUT, FAM_CONTRACT, FAM_N };
+
+struct ProfRec {
+  int fam;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+
+struct qcd_ctx {
+  int prof_on = 0;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> evpool;
+  Geom g;
+  int dims[4];     // T, X, Y, Z as given by the caller
+  cudaStream_t stream;
+  double kappa = 0, csw = 0;
+  int have_gauge = 0;
+  qcd_solver_params params;
+  // fields
+  DevBuf gaugeD, gaugeF, cloverD, cloverF;
+  // workspaces (grown on demand, kept until destroy)
+  DevBuf wsD[8];      // FP64 spinors (nrhs each)
+  DevBuf wsF[8];      // FP32 spinors
+  DevBuf basisF;      // Krylov basis phi/chi (FP32)
+  DevBuf basisD;      // Krylov basis for the all-FP64 policy
+  DevBuf red;         // reduction partials
+  DevBuf scal;        // device scalars of the solver
+  DevBuf contract;    // per-site contraction values
+  DevBuf stage;       // staging for host <-> device copies
+  double* host_scal = nullptr;   // pinned mirror of scalars
+  size_t host_scal_bytes = 0;
+};
+
+// Brackets the launches issued in its scope with CUDA events when profiling
+// is enabled; bytes and flops are the algorithmic counts of those launches.
+struct ProfScope {
+  qcd_ctx* c;
+  int idx;
+  ProfScope(qcd_ctx* c, int fam, double bytes, double flops);
+  ~ProfScope();
+};
+
+// --------------------------------------------------------------------------
+// Internal entry points shared between the .cu files
+// --------------------------------------------------------------------------
+qcd_status layout_gauge_import(qcd_ctx* c, const double* U_dev);
+qcd_status layout_clover_build(qcd_ctx* c);
+// canonical [rhs][V][4][3] complex FP64 <-> internal spinor of precision prec (0 FP64, 1 FP32)
+qcd_status layout_spinor_import(qcd_ctx* c, const double* in, void* out, int prec, int nrhs);
+qcd_status layout_spinor_export(qcd_ctx* c, const void* in, double* out, int prec, int nrhs);
+qcd_status clover_export(qcd_ctx* c, double* out_dev);
+
+// out = D in (or D^+), internal layout, precision prec; mask may be null,
+// nactive = number of unmasked right-hand sides (for the timing records)
+qcd_status dslash_apply(qcd_ctx* c, const void* in, void* out, int prec, int nrhs, int dagger, const int* mask,
+                        int nactive);
+
+// reductions / vector ops (internal layouts; n = 12 V complex per rhs)
+qcd_status blas_norm2(qcd_ctx* c, const void* x, int prec, int nrhs, double* out_dev, const int* mask);
+qcd_status blas_dot(qcd_ctx* c, const void* x, int precx, const void* y, int precy, int nrhs, double* out_dev,
+                    const int* mask);
+qcd_status blas_convert(qcd_ctx* c, const void* in, int pin, void* out, int pout, int nrhs, const int* mask);
+// y_r += sign * sum_{j<nx} coef[j*nrhs + r] x_{j,r}; x_j at xbase + j*xstride bytes
+qcd_status blas_multi_caxpy(qcd_ctx* c, void* y, int py, const void* xbase, int px, int nx, size_t xstride,
+                            const double* coef_dev, double sign, int nrhs, const int* mask);
+qcd_status blas_scale(qcd_ctx* c, void* x, int px, const double* sc_dev, int nrhs, const int* mask);
+// out = x - y
+qcd_status blas_xmy(qcd_ctx* c, const void* x, const void* y, void* out, int prec, int nrhs, const int* mask);
+
+// SAP preconditioner: psi = M_SAP rho (rho is overwritten), precision prec
+qcd_status sap_apply(qcd_ctx* c, void* rho, void* psi, void* delta, int prec, int nrhs, const int* mask,
+                     int nactive);
+
+size_t spinor_bytes(const qcd_ctx* c, int prec);

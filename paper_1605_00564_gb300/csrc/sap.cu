@@ -1,0 +1,260 @@
+// Schwarz alternating procedure (Sec. 2.2).
+//
+// The lattice is split into blocks of extent b = (bt, bx, by, bz) coloured
+// as a checkerboard (colour = parity of the block coordinates); D_Omega is the
+// operator restricted to the black blocks with the hops that leave a block
+// dropped (Dirichlet), D_dOmega* the hops from Omega into the white blocks.
+// n_cy cycles, each visiting all black then all white blocks, applied to
+// psi = 0 give M_SAP = K sum_{nu<n_cy} (1 - D K)^nu.
+//
+// Residual form of a half-cycle on colour c (rho = eta - D psi):
+//   on every block L of colour c:  x = approx D_L^-1 rho_L (n_mr MR steps from 0),
+//                                   psi_L += x,  rho_L = rho_L - D_L x,  delta_L = x
+//   on the neighbouring sites y of the other colour: rho(y) -= (D delta)(y)
+// The last line touches only blocks of the other colour, which are the next
+// half-cycle's blocks, so it is applied there as a gather at the start of the
+// next sweep: each site at a block face adds kappa * hop(delta) from the
+// neighbouring block (delta of the previous half-cycle).  No two CTAs write
+// the same word, so the result does not depend on scheduling.
+//
+// One CTA per block and right-hand side, one thread per block site; the
+// block's residual lives in shared memory across the MR steps, the solution
+// increment x in registers.
+#include "qcd_internal.cuh"
+
+namespace {
+
+struct SapGeom {
+  int b[4];     // block extents by direction (t, x, y, z)
+  int nb[4];    // blocks per direction
+  int lst[4];   // local stride of direction mu inside a block
+  int vb;       // block volume
+};
+
+template <typename R>
+__device__ inline Spinor<R> smem_load(const Cplx<R>* r_s, int vb, int l) {
+  Spinor<R> o;
+#pragma unroll
+  for (int k = 0; k < 12; k++) o.c[k] = r_s[k * vb + l];
+  return o;
+}
+template <typename R>
+__device__ inline void smem_store(Cplx<R>* r_s, int vb, int l, const Spinor<R>& v) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) r_s[k * vb + l] = v.c[k];
+}
+
+// p += scale * (hops of the block operator inside the block, applied to r_s)
+template <typename F, int MU>
+__device__ inline void block_hop(Spinor<typename F::R>& p, const Cplx<typename F::R>* r_s, const SapGeom& sg,
+                                 const void* gauge, const Geom& g, int s, int l, const int lc[4],
+                                 typename F::R scale) {
+  using R = typename F::R;
+  if (lc[MU] < sg.b[MU] - 1) {
+    HalfSpinor<R> h = project<MU, -1>(smem_load(r_s, sg.vb, l + sg.lst[MU]));
+    h = su3_mul(F::load_link(gauge, g.V, MU, s), h);
+    accum_recon<MU, -1>(p, h, scale);
+  }
+  if (lc[MU] > 0) {
+    HalfSpinor<R> h = project<MU, +1>(smem_load(r_s, sg.vb, l - sg.lst[MU]));
+    h = su3_dag_mul(F::load_link(gauge, g.V, MU, s - g.stride[MU]), h);
+    accum_recon<MU, +1>(p, h, scale);
+  }
+}
+
+// r += scale * (hops from delta on the neighbouring blocks, across this block's faces)
+template <typename F, int MU>
+__device__ inline void face_hop(Spinor<typename F::R>& hop, const char* delta, const SapGeom& sg, const void* gauge,
+                                const Geom& g, int s, const int c[4], const int lc[4], typename F::R scale) {
+  using R = typename F::R;
+  if (lc[MU] == sg.b[MU] - 1) {
+    int sf = site_fwd(g, s, c, MU);
+    R sign = (MU == 0 && c[0] == g.L[0] - 1) ? (R)g.bc_t * scale : scale;
+    HalfSpinor<R> h = project<MU, -1>(F::load_spinor(delta, g.V, sf));
+    h = su3_mul(F::load_link(gauge, g.V, MU, s), h);
+    accum_recon<MU, -1>(hop, h, sign);
+  }
+  if (lc[MU] == 0) {
+    int sb = site_bwd(g, s, c, MU);
+    R sign = (MU == 0 && c[0] == 0) ? (R)g.bc_t * scale : scale;
+    HalfSpinor<R> h = project<MU, +1>(F::load_spinor(delta, g.V, sb));
+    h = su3_dag_mul(F::load_link(gauge, g.V, MU, sb), h);
+    accum_recon<MU, +1>(hop, h, sign);
+  }
+}
+
+template <typename R>
+__device__ inline R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename F, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(char* __restrict__ rho, char* __restrict__ psi, char* __restrict__ delta,
+                            const void* __restrict__ gauge, const void* __restrict__ clover, Geom g, SapGeom sg,
+                            int colour, int gather, int psi_init, typename F::R kappa, int nmr, int nrhs,
+                            const int* mask) {
+  using R = typename F::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<R>* r_s = (Cplx<R>*)smem_raw;
+  __shared__ R red[3][32];
+
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const size_t off = (size_t)rhs * F::spinor_bytes * g.V;
+  rho += off;
+  psi += off;
+  delta += off;
+
+  // which block: the blockIdx.x-th block of this colour
+  const int nbx2 = sg.nb[1] >> 1;
+  int q = blockIdx.x / nbx2;
+  const int j = blockIdx.x - q * nbx2;
+  const int by = q % sg.nb[2];
+  q /= sg.nb[2];
+  const int bz = q % sg.nb[3];
+  const int bt = q / sg.nb[3];
+  const int bx = 2 * j + ((colour + bt + bz + by) & 1);
+
+  const int l = threadIdx.x;
+  int lc[4], c[4];
+  {
+    int r = l;
+    lc[1] = r % sg.b[1]; r /= sg.b[1];
+    lc[2] = r % sg.b[2]; r /= sg.b[2];
+    lc[3] = r % sg.b[3];
+    lc[0] = r / sg.b[3];
+  }
+  c[0] = bt * sg.b[0] + lc[0];
+  c[1] = bx * sg.b[1] + lc[1];
+  c[2] = by * sg.b[2] + lc[2];
+  c[3] = bz * sg.b[3] + lc[3];
+  const int s = ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
+
+  // pending boundary update from the previous half-cycle
+  Spinor<R> r = F::load_spinor(rho, g.V, s);
+  if (gather) {
+    face_hop<F, 0>(r, delta, sg, gauge, g, s, c, lc, kappa);
+    face_hop<F, 1>(r, delta, sg, gauge, g, s, c, lc, kappa);
+    face_hop<F, 2>(r, delta, sg, gauge, g, s, c, lc, kappa);
+    face_hop<F, 3>(r, delta, sg, gauge, g, s, c, lc, kappa);
+  }
+  smem_store(r_s, sg.vb, l, r);
+
+  Spinor<R> x;
+#pragma unroll
+  for (int k = 0; k < 12; k++) x.c[k] = cmk((R)0, (R)0);
+
+  const int warp = l >> 5, lane = l & 31, nw = (sg.vb + 31) >> 5;
+  for (int step = 0; step < nmr; step++) {
+    __syncthreads();
+    // p = D_L r
+    Spinor<R> p = clover_apply<F>(clover, g.V, s, r);
+    block_hop<F, 0>(p, r_s, sg, gauge, g, s, l, lc, -kappa);
+    block_hop<F, 1>(p, r_s, sg, gauge, g, s, l, lc, -kappa);
+    block_hop<F, 2>(p, r_s, sg, gauge, g, s, l, lc, -kappa);
+    block_hop<F, 3>(p, r_s, sg, gauge, g, s, l, lc, -kappa);
+    // alpha = (p, r) / (p, p) over the block
+    R pr_re = 0, pr_im = 0, pp = 0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      pr_re += p.c[k].re * r.c[k].re + p.c[k].im * r.c[k].im;
+      pr_im += p.c[k].re * r.c[k].im - p.c[k].im * r.c[k].re;
+      pp += p.c[k].re * p.c[k].re + p.c[k].im * p.c[k].im;
+    }
+    pr_re = warp_sum(pr_re);
+    pr_im = warp_sum(pr_im);
+    pp = warp_sum(pp);
+    if (lane == 0) {
+      red[0][warp] = pr_re;
+      red[1][warp] = pr_im;
+      red[2][warp] = pp;
+    }
+    __syncthreads();
+    R a_re = 0, a_im = 0, n2 = 0;
+    for (int w = 0; w < nw; w++) {
+      a_re += red[0][w];
+      a_im += red[1][w];
+      n2 += red[2][w];
+    }
+    Cplx<R> alpha = n2 > (R)0 ? cmk(a_re / n2, a_im / n2) : cmk((R)0, (R)0);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      x.c[k] = x.c[k] + alpha * r.c[k];
+      r.c[k] = r.c[k] - alpha * p.c[k];
+    }
+    __syncthreads();
+    smem_store(r_s, sg.vb, l, r);
+  }
+
+  if (psi_init) {
+    F::store_spinor(psi, g.V, s, x);
+  } else {
+    Spinor<R> y = F::load_spinor(psi, g.V, s);
+#pragma unroll
+    for (int k = 0; k < 12; k++) y.c[k] = y.c[k] + x.c[k];
+    F::store_spinor(psi, g.V, s, y);
+  }
+  F::store_spinor(rho, g.V, s, r);
+  F::store_spinor(delta, g.V, s, x);
+}
+
+template <typename F>
+qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const void* gauge, const void* clover,
+                         int nrhs, const int* mask, int nactive) {
+  const qcd_solver_params& P = c->params;
+  SapGeom sg;
+  sg.vb = 1;
+  for (int mu = 0; mu < 4; mu++) {
+    sg.b[mu] = P.block[mu];
+    sg.nb[mu] = c->g.L[mu] / sg.b[mu];
+    sg.vb *= sg.b[mu];
+  }
+  sg.lst[1] = 1;
+  sg.lst[2] = sg.b[1];
+  sg.lst[3] = sg.b[1] * sg.b[2];
+  sg.lst[0] = sg.b[1] * sg.b[2] * sg.b[3];
+  const int nblocks = sg.nb[0] * sg.nb[1] * sg.nb[2] * sg.nb[3];
+  const size_t smem = (size_t)12 * sg.vb * sizeof(Cplx<typename F::R>);
+  // the register budget per thread follows from the block volume; FP32 fits
+  // 128 registers without spilling, so 256-site blocks run two CTAs per SM
+  constexpr int MINB256 = sizeof(typename F::R) == 4 ? 2 : 1;
+  auto kern = sg.vb <= 256   ? k_sap_sweep<F, 256, MINB256>
+              : sg.vb <= 512 ? k_sap_sweep<F, 512, 1>
+                             : k_sap_sweep<F, 1024, 1>;
+  QCD_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(nblocks / 2, nrhs);
+  // Algorithmic cost of one half-cycle per active site and RHS: rho read and
+  // written, psi read and written (written only in the first cycle), delta
+  // written, the neighbouring blocks' delta read once per face hop, the
+  // site's 4 links and clover term; per MR step the block operator (its
+  // internal hops and the clover term) plus the MR update (24 complex
+  // multiply-adds), and one hop per face direction for the gather.
+  double face = 0;
+  for (int mu = 0; mu < 4; mu++) face += 2.0 / sg.b[mu];
+  const double sb = (double)F::spinor_bytes, lb = (double)F::link_bytes, cb = (double)F::clover_bytes;
+  const double half = c->g.V / 2.0;
+  const double flops_site = P.nmr * (1320.0 * (1.0 - face / 8.0) + 504.0 + 192.0) + 165.0 * face;
+  const int fam = sizeof(typename F::R) == 8 ? FAM_SAP_D : FAM_SAP_F;
+  for (int cy = 0; cy < P.ncy; cy++)
+    for (int col = 0; col < 2; col++) {
+      const double bytes_site = sb * (2 + (cy == 0 ? 1 : 2) + 1 + face) + 4 * lb + cb;
+      ProfScope ps(c, fam, half * nactive * bytes_site, half * nactive * flops_site);
+      kern<<<grid, sg.vb, smem, c->stream>>>(rho, psi, delta, gauge, clover, c->g, sg, col, !(cy == 0 && col == 0),
+                                             cy == 0, (typename F::R)c->kappa, P.nmr, nrhs, mask);
+      QCD_CUDA_OK(cudaGetLastError());
+    }
+  return QCD_OK;
+}
+
+}  // namespace
+
+qcd_status sap_apply(qcd_ctx* c, void* rho, void* psi, void* delta, int prec, int nrhs, const int* mask,
+                     int nactive) {
+  if (prec == QCD_PREC_F64)
+    return launch_sweeps<FieldsD>(c, (char*)rho, (char*)psi, (char*)delta, c->gaugeD.p, c->cloverD.p, nrhs, mask,
+                                  nactive);
+  return launch_sweeps<FieldsF>(c, (char*)rho, (char*)psi, (char*)delta, c->gaugeF.p, c->cloverF.p, nrhs, mask,
+                                nactive);
+}

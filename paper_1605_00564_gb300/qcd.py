@@ -1,0 +1,245 @@
+"""Thin Python binding of the C-ABI in include/qcd.h (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libqcd_gb300.so``.  Device buffers are torch tensors (complex128,
+canonical layouts); the context is bound to a torch CUDA stream.  If the
+library is missing the import of this module still works, but creating a
+``Lattice`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqcd_gb300.so")
+
+PREC = {"f64": 0, "f32": 1}
+
+STATUS = {
+    0: "QCD_OK", 1: "QCD_ERR_ARG", 2: "QCD_ERR_CUDA", 3: "QCD_ERR_OOM", 4: "QCD_ERR_NOT_CONVERGED",
+    5: "QCD_ERR_BREAKDOWN", 6: "QCD_ERR_NONFINITE", 7: "QCD_ERR_TIMEOUT", 8: "QCD_ERR_STATE",
+}
+
+# every symbol include/qcd.h declares
+EXPORTS = (
+    "qcd_status_string", "qcd_last_error", "qcd_create", "qcd_destroy", "qcd_load_gauge",
+    "qcd_default_params", "qcd_set_params", "qcd_apply_dirac", "qcd_apply_sap", "qcd_solve",
+    "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_get_clover", "qcd_profile_enable", "qcd_profile_read",
+)
+
+
+class QcdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [
+        ("block", ctypes.c_int * 4), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int), ("nkv", ctypes.c_int),
+        ("max_outer", ctypes.c_int), ("restart_drop", ctypes.c_double), ("precision", ctypes.c_int),
+        ("rhs_tile", ctypes.c_int),
+    ]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class RhsStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"status": STATUS.get(self.status, self.status), "outer_iters": self.outer_iters,
+                "restarts": self.restarts, "true_rel_residual": self.true_rel_residual}
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libqcd_gb300.so and declare the signatures; raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libqcd_gb300.so not found at %s: run __graft_entry__.build() first "
+                           "(the library has no CPU fallback)" % path)
+    L = ctypes.CDLL(path)
+    vp, ip, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), \
+        ctypes.c_int, ctypes.c_double
+    L.qcd_status_string.restype = ctypes.c_char_p
+    L.qcd_status_string.argtypes = [i]
+    L.qcd_last_error.restype = ctypes.c_char_p
+    L.qcd_last_error.argtypes = []
+    L.qcd_create.argtypes = [ctypes.POINTER(vp), ip, vp]
+    L.qcd_destroy.argtypes = [vp]
+    L.qcd_destroy.restype = None
+    L.qcd_load_gauge.argtypes = [vp, vp, i, d, d, i]
+    L.qcd_default_params.argtypes = [ctypes.POINTER(SolverParams)]
+    L.qcd_default_params.restype = None
+    L.qcd_set_params.argtypes = [vp, ctypes.POINTER(SolverParams)]
+    L.qcd_apply_dirac.argtypes = [vp, vp, vp, i, i, i]
+    L.qcd_apply_sap.argtypes = [vp, vp, vp, i, i]
+    L.qcd_solve.argtypes = [vp, vp, vp, i, dp, ctypes.POINTER(RhsStats)]
+    L.qcd_nucleon_2pt.argtypes = [vp, vp, ip, dp, i]
+    L.qcd_ama_nucleon_2pt.argtypes = [vp, ip, i, i, d, d, dp, dp, ctypes.POINTER(RhsStats)]
+    L.qcd_get_clover.argtypes = [vp, vp]
+    L.qcd_profile_enable.argtypes = [vp, i]
+    L.qcd_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), i, ip]
+    for name in EXPORTS:
+        if name not in ("qcd_status_string", "qcd_last_error", "qcd_destroy", "qcd_default_params"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status, allow=()):
+    if status != 0 and status not in allow:
+        raise QcdError(status, _lib.qcd_last_error().decode(errors="replace"))
+    return status
+
+
+def _dev_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Lattice:
+    """A lattice context: dims = (T, X, Y, Z)."""
+
+    def __init__(self, dims, stream=None):
+        import torch
+        L = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the Wilson-clover library runs on the GPU only")
+        self.dims = tuple(int(x) for x in dims)
+        self.T, self.X, self.Y, self.Z = self.dims
+        self.V = self.T * self.X * self.Y * self.Z
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = ctypes.c_void_p()
+        _check(L.qcd_create(ctypes.byref(self._ctx), (ctypes.c_int * 4)(*self.dims),
+                            ctypes.c_void_p(self.stream.cuda_stream)))
+        self.params = SolverParams()
+        L.qcd_default_params(ctypes.byref(self.params))
+        self.time_bc = -1
+
+    # ----------------------------------------------------------------------
+    def close(self):
+        if self._ctx:
+            _lib.qcd_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spinor_shape(self, nrhs=None):
+        s = (self.T, self.Z, self.Y, self.X, 4, 3)
+        return s if nrhs is None else (nrhs,) + s
+
+    # ----------------------------------------------------------------------
+    def load_gauge(self, U, csw, kappa, time_bc=-1):
+        """U: numpy complex128 (host) or torch complex128 CUDA tensor, shape (T,Z,Y,X,4,3,3)."""
+        import torch
+        self.time_bc = int(time_bc)
+        if isinstance(U, torch.Tensor):
+            U = U.contiguous()
+            st = _lib.qcd_load_gauge(self._ctx, _dev_ptr(U), 1, float(csw), float(kappa), int(time_bc))
+        else:
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+            st = _lib.qcd_load_gauge(self._ctx, U.ctypes.data_as(ctypes.c_void_p), 0, float(csw), float(kappa),
+                                     int(time_bc))
+        _check(st)
+
+    def set_params(self, **kw):
+        p = SolverParams()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(self.params), ctypes.sizeof(p))
+        for k, v in kw.items():
+            if k == "block":
+                p.block = (ctypes.c_int * 4)(*v)
+            elif k == "precision":
+                p.precision = PREC[v] if isinstance(v, str) else int(v)
+            else:
+                setattr(p, k, v)
+        _check(_lib.qcd_set_params(self._ctx, ctypes.byref(p)))
+        self.params = p
+
+    # ----------------------------------------------------------------------
+    def apply_dirac(self, psi, dagger=False, precision="f64"):
+        import torch
+        psi = psi.contiguous()
+        n = psi.shape[0] if psi.dim() == 7 else 1
+        out = torch.empty_like(psi)
+        _check(_lib.qcd_apply_dirac(self._ctx, _dev_ptr(psi), _dev_ptr(out), n, int(bool(dagger)), PREC[precision]))
+        return out
+
+    def apply_sap(self, eta, precision="f32"):
+        import torch
+        eta = eta.contiguous()
+        n = eta.shape[0] if eta.dim() == 7 else 1
+        out = torch.empty_like(eta)
+        _check(_lib.qcd_apply_sap(self._ctx, _dev_ptr(eta), _dev_ptr(out), n, PREC[precision]))
+        return out
+
+    def solve(self, eta, tol, psi0=None, allow_not_converged=False):
+        """Solve D psi = eta; returns (psi, [stats dict per RHS])."""
+        import torch
+        eta = eta.contiguous()
+        n = eta.shape[0] if eta.dim() == 7 else 1
+        psi = torch.zeros_like(eta) if psi0 is None else psi0.clone().contiguous()
+        tols = (ctypes.c_double * n)(*([float(tol)] * n if np.isscalar(tol) else [float(x) for x in tol]))
+        stats = (RhsStats * n)()
+        st = _lib.qcd_solve(self._ctx, _dev_ptr(eta), _dev_ptr(psi), n, tols, stats)
+        _check(st, allow=(4,) if allow_not_converged else ())
+        return psi, [s.as_dict() for s in stats]
+
+    def nucleon_2pt(self, prop, src, precision="f64"):
+        """C[parity, t] (complex, host numpy) from a 12-spinor point-source propagator."""
+        prop = prop.contiguous()
+        out = np.zeros((2, self.T, 2), dtype=np.float64)
+        _check(_lib.qcd_nucleon_2pt(self._ctx, _dev_ptr(prop), (ctypes.c_int * 4)(*src),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), PREC[precision]))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def ama_nucleon_2pt(self, srcs, n_exact, sloppy_tol, exact_tol, allow_not_converged=False):
+        """AMA nucleon two-point function; returns (ama[2,T], all[n_src+n_exact,2,T], stats)."""
+        srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32).reshape(-1, 4))
+        ns = srcs.shape[0]
+        ama = np.zeros((2, self.T, 2))
+        allc = np.zeros((ns + n_exact, 2, self.T, 2))
+        stats = (RhsStats * (12 * (ns + n_exact)))()
+        st = _lib.qcd_ama_nucleon_2pt(self._ctx, srcs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ns,
+                                      int(n_exact), float(sloppy_tol), float(exact_tol),
+                                      ama.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      allc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats)
+        _check(st, allow=(4,) if allow_not_converged else ())
+        return ama[..., 0] + 1j * ama[..., 1], allc[..., 0] + 1j * allc[..., 1], [s.as_dict() for s in stats]
+
+    def profile(self, on=True):
+        """Start (clearing old records) or stop recording kernel times."""
+        _check(_lib.qcd_profile_enable(self._ctx, int(bool(on))))
+
+    def profile_read(self):
+        """{family: {launches, ms, bytes, flops}} since the last read; clears the records."""
+        buf = (KernelTime * 16)()
+        n = ctypes.c_int()
+        _check(_lib.qcd_profile_read(self._ctx, buf, 16, ctypes.byref(n)))
+        return {buf[k].name.decode(): {"launches": buf[k].launches, "ms": buf[k].ms, "bytes": buf[k].bytes,
+                                       "flops": buf[k].flops} for k in range(n.value)}
+
+    def get_clover(self):
+        """A(x) as a CUDA complex128 tensor [V, 2, 6, 6]."""
+        import torch
+        out = torch.empty((self.V, 2, 6, 6), dtype=torch.complex128, device="cuda")
+        _check(_lib.qcd_get_clover(self._ctx, _dev_ptr(out)))
+        return out

@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/qcd.h declares.  No compute call is made (no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "qcd.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(qcd_[a-z0-9_]+)\s*\(", hdr)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1605_00564_gb300 import build, qcd
+    build.build()
+    return qcd.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("qcd_create", "qcd_load_gauge", "qcd_apply_dirac", "qcd_apply_sap", "qcd_solve",
+              "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_destroy"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1605_00564_gb300 import qcd
+    names = _declared()
+    assert set(names) == set(qcd.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_host_only_calls(lib):
+    from paper_1605_00564_gb300 import qcd
+    p = qcd.SolverParams()
+    lib.qcd_default_params(ctypes.byref(p))
+    assert list(p.block) == [4, 4, 4, 4] and p.ncy == 5 and p.nmr == 4 and p.nkv == 16
+    assert lib.qcd_status_string(0) == b"ok"
+    assert lib.qcd_status_string(4) == b"solver did not converge"
+    # argument errors are reported before any device work
+    ctx = ctypes.c_void_p()
+    assert lib.qcd_create(ctypes.byref(ctx), (ctypes.c_int * 4)(16, 1, 8, 8), None) == 1
+    assert b"extent" in lib.qcd_last_error()
+
+
+def test_library_is_sm103a():
+    from paper_1605_00564_gb300 import build
+    assert "compute_103a,code=sm_103a" in build.ARCH

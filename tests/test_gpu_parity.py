@@ -1,0 +1,113 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Tolerances (norm-wise relative unless stated):
+  FP64 operator        1e-13   (same formula, different summation order)
+  FP32 operator        2e-6    (single-precision rounding of ~20 terms)
+  clover term, FP64    1e-14   (max abs)
+  SAP FP64 vs oracle   1e-11   (identical MR algorithm in FP64)
+  SAP FP32 vs oracle   2e-4    (MR step lengths in FP32)
+  exact solve          oracle-computed residual <= 1.1e-10, solution <= 1e-8
+  sloppy solve         oracle-computed residual <= 1e-3
+  contraction FP64     1e-12 of max |C|; FP32 2e-5 of max |C|
+"""
+import numpy as np
+import pytest
+
+from gpu_util import make_lattice, rel, to_dev, to_host
+from paper_1605_00564_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    return make_lattice("small_8c16")
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    # extents that are not multiples of the CTA size in any direction
+    return make_lattice((6, 6, 10, 2), eps=0.4, csw=1.7, kappa=0.128, seed=77)
+
+
+@pytest.mark.parametrize("which", ["small", "ragged"])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dirac_fp64(request, which, dagger):
+    lat, op, _ = request.getfixturevalue(which)
+    psi = synth.random_spinor(lat.dims, 3, nrhs=3)
+    out = to_host(lat.apply_dirac(to_dev(psi), dagger=dagger, precision="f64"))
+    ref = np.stack([op.D(p, dagger=dagger) for p in psi])
+    assert rel(out, ref) < 1e-13
+
+
+@pytest.mark.parametrize("which", ["small", "ragged"])
+def test_dirac_fp32(request, which):
+    lat, op, _ = request.getfixturevalue(which)
+    psi = synth.random_spinor(lat.dims, 4, nrhs=2)
+    out = to_host(lat.apply_dirac(to_dev(psi), precision="f32"))
+    ref = np.stack([op.D(p) for p in psi])
+    assert rel(out, ref) < 2e-6
+
+
+def test_dirac_periodic_time():
+    lat, op, _ = make_lattice((4, 4, 4, 6), eps=0.3, csw=1.0, kappa=0.125, seed=5, bc_t=1)
+    psi = synth.random_spinor(lat.dims, 9)
+    out = to_host(lat.apply_dirac(to_dev(psi[None]), precision="f64"))[0]
+    assert rel(out, op.D(psi)) < 1e-13
+
+
+def test_clover_field(small):
+    lat, op, _ = small
+    A = to_host(lat.get_clover()).reshape(lat.T, lat.Z, lat.Y, lat.X, 2, 6, 6)
+    ref = op.C + np.eye(12)
+    assert np.abs(A[..., 0, :, :] - ref[..., :6, :6]).max() < 1e-14
+    assert np.abs(A[..., 1, :, :] - ref[..., 6:, 6:]).max() < 1e-14
+    assert np.abs(ref[..., :6, 6:]).max() == 0.0
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 2e-4)])
+@pytest.mark.parametrize("block", [(4, 4, 4, 4), (8, 4, 4, 4), (4, 2, 4, 2)])
+def test_sap_matches_oracle(small, prec, tol, block):
+    from oracle.sap import SAP
+    lat, op, _ = small
+    lat.set_params(block=block, ncy=3, nmr=4)
+    eta = synth.random_spinor(lat.dims, 11, nrhs=2)
+    out = to_host(lat.apply_sap(to_dev(eta), precision=prec))
+    s = SAP(op, block, ncy=3, nmr=4)
+    ref = np.stack([s.apply(e) for e in eta])
+    assert rel(out, ref) < tol
+
+
+def test_solve_exact_and_sloppy(small):
+    from oracle.solve import gcr
+    lat, op, _ = small
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32")
+    src = synth.point_sources(lat.dims, (0, 0, 0, 0))
+    eta = to_dev(src)
+    psi, st = lat.solve(eta, 1e-10)
+    psi = to_host(psi)
+    for r in range(12):
+        res = np.linalg.norm(src[r] - op.D(psi[r])) / np.linalg.norm(src[r])
+        assert st[r]["status"] == "QCD_OK"
+        assert res <= 1.1e-10, (r, res, st[r])
+    x, it, res = gcr(op, src[0], tol=1e-13)
+    assert rel(psi[0], x) < 1e-8
+    psis, sts = lat.solve(eta, 1e-3)
+    psis = to_host(psis)
+    for r in range(12):
+        res = np.linalg.norm(src[r] - op.D(psis[r])) / np.linalg.norm(src[r])
+        assert res <= 1e-3, (r, res)
+    # the sloppy solve needs fewer preconditioner applications
+    assert max(s["outer_iters"] for s in sts) < min(s["outer_iters"] for s in st)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_nucleon_contraction(small, prec, tol):
+    from oracle import nucleon
+    lat, op, _ = small
+    rng = np.random.default_rng(3)
+    prop = rng.standard_normal(lat.spinor_shape(12) + (2,)) @ np.array([1, 1j])
+    src = (3, 4, 0, 4)
+    out = lat.nucleon_2pt(to_dev(prop), src, precision=prec)
+    ref = nucleon.two_point(prop, src[0])
+    assert np.abs(out - ref).max() <= tol * np.abs(ref).max()
