@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark: batched mixed-precision AMA nucleon two-point function, 32^3x64.
+
+One step is the whole hot path on one gauge configuration, one call of
+qcd_ama_nucleon_2pt: the 12 spin-colour point sources at each of N_G = 8
+block-preserving source positions solved with SAP-preconditioned flexible
+GCR to the sloppy tolerance 1e-3, the 12 sources of the first position also
+solved to 1e-10 (N_org = 1), the nucleon contraction of all 9 propagators
+and the AMA combination.  value = solves per second, a solve being one
+spin-colour right-hand side brought to its tolerance (108 per step).
+
+Timing: W warm-up steps, then K steps between CUDA events on the library's
+stream, with a barrier and a synchronize on both sides; the maximum over
+ranks is reported.  The inputs (FP32 gauge 403 MB + clover 604 MB per
+lattice) are larger than L2, so no flush is needed between steps.
+
+--impl reference times the oracle (plain FP64 numpy, unpreconditioned GCR) on
+a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AMA solves/sec on 32^3x64 (batched mixed vs plain FP64); Dslash HBM GB/s vs peak"
+UNIT = "solves/s"
+WORKLOAD = dict(name="prod_32c64", n_g=8, n_org=1, sloppy_tol=1e-3, exact_tol=1e-10,
+                block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, sap_half=1, restart_drop=1e-5, max_outer=4000)
+FP32_ALU_TFLOPS_PER_GHZ = 152 * 128 * 2 / 1000.0   # SMs x FP32 lanes x 2 flops per FMA
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "_fallback": True}
+
+
+def workload_config():
+    from paper_1605_00564_gb300 import synth
+    cfg = dict(synth.CONFIGS[WORKLOAD["name"]])
+    srcs = synth.ama_source_shifts(cfg["dims"], WORKLOAD["n_g"])
+    return cfg, srcs
+
+
+def config_json(cfg):
+    T, X, Y, Z = cfg["dims"]
+    return {
+        "workload": "AMA nucleon 2pt, %dx%d^3 (T=%d), N_G=%d sloppy (tol %g) + N_org=%d exact (tol %g), "
+                    "12 spin-colour RHS each" % (X, X, T, WORKLOAD["n_g"], WORKLOAD["sloppy_tol"], WORKLOAD["n_org"],
+                                                 WORKLOAD["exact_tol"]),
+        "lattice": [T, X, Y, Z], "kappa": cfg["kappa"], "csw": cfg["csw"], "gauge": "U=exp(i*%g*H) seeded" % cfg["eps"],
+        "solver": "FGCR(nkv=%d, restart_drop=%g) + SAP(block %s, ncy=%d, nmr=%d, FP32, %s block copies)" % (
+            WORKLOAD["nkv"], WORKLOAD["restart_drop"], "x".join(map(str, WORKLOAD["block"])), WORKLOAD["ncy"],
+            WORKLOAD["nmr"], "FP16" if WORKLOAD["sap_half"] else "FP32"),
+        "rhs_per_step": 12 * (WORKLOAD["n_g"] + WORKLOAD["n_org"]),
+        "l2": "inputs larger than L2 (FP32 gauge+clover 1.0 GB), no flush",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(budget_s=20.0):
+    """Unpreconditioned oracle GCR on one right-hand side of the workload
+    (source at the first AMA position, spin 0 colour 0) on the host cores for
+    about budget_s seconds.  Returns (solves/s, description, threads): the
+    time per solve is the time per GCR iteration times the iterations needed
+    for the workload's mix of tolerances, extrapolated geometrically from the
+    residual reduction of the sampled iterations."""
+    from oracle.dirac import Operator, inner, norm
+    from paper_1605_00564_gb300 import synth
+    cfg, srcs = workload_config()
+    U = synth.gauge_field(cfg["dims"], cfg["eps"], cfg["seed"])
+    t0w, t0c = time.perf_counter(), time.process_time()
+    op = Operator(U, cfg["kappa"], cfg["csw"], -1)
+    eta = synth.point_source(cfg["dims"], srcs[0], 0, 0)
+    # plain GCR iterations (same steps as oracle.solve.gcr), timed one by one
+    r = eta.copy()
+    ps, qs = [], []
+    eta_n = norm(eta)
+    its, res = 0, [1.0]
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s or its < 2:
+        p = r.copy()
+        q = op.D(p)
+        for pj, qj in zip(ps, qs):
+            c = inner(qj, q)
+            q = q - c * qj
+            p = p - c * pj
+        nq = norm(q)
+        p, q = p / nq, q / nq
+        ps.append(p)
+        qs.append(q)
+        r = r - inner(q, r) * q
+        its += 1
+        res.append(norm(r) / eta_n)
+    t_iter = (time.perf_counter() - t_start) / its
+    wall, cpu = time.perf_counter() - t0w, time.process_time() - t0c
+    rate = max(res[-1], 1e-300) ** (1.0 / its)          # residual factor per iteration
+    n_s = np.log(WORKLOAD["sloppy_tol"]) / np.log(rate) if rate < 1 else float("inf")
+    n_e = np.log(WORKLOAD["exact_tol"]) / np.log(rate) if rate < 1 else float("inf")
+    t_step = t_iter * (12 * WORKLOAD["n_g"] * n_s + 12 * WORKLOAD["n_org"] * n_e)
+    solves = 12 * (WORKLOAD["n_g"] + WORKLOAD["n_org"])
+    value = solves / t_step if np.isfinite(t_step) and t_step > 0 else 0.0
+    desc = ("%d oracle GCR iterations (unpreconditioned, FP64 numpy) on one RHS of the 32^3x64 workload, %.2f s per "
+            "iteration; residual factor %.4f per iteration extrapolated to %.0f iterations at tol %g and %.0f at tol %g; "
+            "value = %d solves / (96 sloppy + 12 exact solve times)" % (
+                its, t_iter, rate, n_s, WORKLOAD["sloppy_tol"], n_e, WORKLOAD["exact_tol"], solves))
+    threads = max(1, int(round(cpu / max(wall, 1e-9))))
+    return value, desc, threads
+
+
+# ---------------------------------------------------------------------------
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def kernel_traffic(family_kernel):
+    """DRAM bytes per unit of the dominant kernel from the committed ncu summary,
+    if it was taken on the current source of that kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[family_kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec if sha == rec.get("source_sha") else None
+
+
+def run_ours(args):
+    import torch
+    from paper_1605_00564_gb300.qcd import Lattice
+    from paper_1605_00564_gb300 import synth
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    cfg, srcs = workload_config()
+    seed = cfg["seed"] + rank                 # each rank: its own configuration
+    U = synth.gauge_field(cfg["dims"], cfg["eps"], seed)
+    lat = Lattice(cfg["dims"])
+    lat.load_gauge(U, cfg["csw"], cfg["kappa"], -1)
+    lat.set_params(block=WORKLOAD["block"], ncy=WORKLOAD["ncy"], nmr=WORKLOAD["nmr"], nkv=WORKLOAD["nkv"],
+                   precision="f32", sap_half=WORKLOAD["sap_half"], restart_drop=WORKLOAD["restart_drop"],
+                   max_outer=WORKLOAD["max_outer"])
+    n_ex = WORKLOAD["n_org"]
+    step = lambda: lat.ama_nucleon_2pt(srcs, n_ex, WORKLOAD["sloppy_tol"], WORKLOAD["exact_tol"])
+    for _ in range(args.warmup):
+        step()
+    stream = lat.stream
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    lat.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = None
+    for _ in range(args.steps):
+        ama, allc, stats = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = lat.profile_read()
+    lat.profile(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    barrier(ws)
+    ms_max = max_over_ranks(ms, ws)
+    solves = 12 * (WORKLOAD["n_g"] + n_ex)
+    value = ws * solves * args.steps / (ms_max / 1e3)
+
+    # end to end through the C-ABI with host buffers: gauge field H2D from
+    # pinned memory, correlators D2H, every step
+    Upin = torch.empty(U.shape, dtype=torch.complex128, pin_memory=True)
+    Upin.numpy()[...] = U
+    Uh = Upin.numpy()
+    n_e2e = max(1, args.steps // 2)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        lat.load_gauge(Uh, cfg["csw"], cfg["kappa"], -1)
+        step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": ws * solves * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes + 16 * len(srcs)),
+           "d2h_bytes_per_step": int(ama.nbytes + allc.nbytes + 12 * (len(srcs) + n_ex) * 24)}
+
+    # Dslash bandwidth (the metric's second part): FP32, 1 and 12 RHS, kernel time
+    pk = peaks()
+    dsl = {}
+    for n in (1, 12):
+        psi = torch.randn(lat.spinor_shape(n), dtype=torch.complex128, device="cuda")
+        lat.apply_dirac(psi, precision="f32")
+        lat.profile(True)
+        for _ in range(10):
+            lat.apply_dirac(psi, precision="f32")
+        p = lat.profile_read()["dslash_f32"]
+        lat.profile(False)
+        gbs = p["bytes"] / p["ms"] / 1e6
+        dsl["f32_nrhs%d" % n] = {"gbs": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 3),
+                                 "us_per_launch": round(1e3 * p["ms"] / p["launches"], 1)}
+        del psi
+    lat.profile(False)
+
+    # plain single-RHS FP64 SAP-GCR at the same accuracy: time per GCR iteration
+    # measured on 10 iterations of one RHS, times the mixed solver's iteration counts
+    plain = None
+    if rank == 0 and not args.skip_plain:
+        lat.set_params(precision="f64", rhs_tile=1, max_outer=10, restart_drop=0.0)
+        e = torch.from_numpy(synth.point_sources(cfg["dims"], srcs[0])[:1]).cuda()
+        lat.solve(e, 1e-12, allow_not_converged=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = lat.solve(e, 1e-12, allow_not_converged=True)
+        torch.cuda.synchronize()
+        t_it = (time.perf_counter() - t0) / max(st[0]["outer_iters"], 1)
+        its = [s["outer_iters"] for s in stats]
+        t_plain = t_it * sum(its)
+        plain = {"value": round(solves / t_plain, 4), "unit": UNIT,
+                 "how": "FP64 SAP-GCR, one RHS at a time: %.1f ms per GCR iteration (10 iterations measured) x the "
+                        "%d GCR iterations the batched mixed solver needed for this step" % (1e3 * t_it, sum(its)),
+                 "mixed_over_plain": round(value / ws / (solves / t_plain), 2)}
+        lat.set_params(precision="f32", rhs_tile=0, max_outer=WORKLOAD["max_outer"],
+                       restart_drop=WORKLOAD["restart_drop"])
+
+    # roofline of the dominant kernel family inside the timed region
+    fam = max(prof, key=lambda k: prof[k]["ms"])
+    f = prof[fam]
+    ridge = FP32_ALU_TFLOPS_PER_GHZ * (clk["sm_mhz"] / 1000.0 if clk else pk.get("sm_max_mhz", 2070) / 1000.0) \
+        * 1e12 / (pk["hbm_gbs"] * 1e9)
+    ai = f["flops"] / max(f["bytes"], 1)
+    per_launch_bytes = f["bytes"] / f["launches"]
+    tr = kernel_traffic(fam)
+    if ai < ridge:
+        achieved = f["bytes"] / f["ms"] / 1e6
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 3)}
+    else:
+        achieved = f["flops"] / f["ms"] / 1e9
+        alu_peak = FP32_ALU_TFLOPS_PER_GHZ * pk.get("sm_max_mhz", 2070) / 1000.0
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / alu_peak, 3)}
+    roof.update({"kernel": fam, "launches": f["launches"], "share_of_step": round(f["ms"] / ms, 3),
+                 "algorithmic_bytes_per_launch": int(per_launch_bytes), "flops_per_byte": round(ai, 2),
+                 "traffic": (int(tr["bytes_per_alg_byte"] * per_launch_bytes) if tr else None),
+                 "peak_source": "MEASURED_PEAKS.json" if not pk.get("_fallback") else "fallback"})
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        v, desc, thr = oracle_sample(args.cpu_budget)
+        cpu = {"value": round(v, 6), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+
+    launches = sum(p["launches"] for p in prof.values())
+    iters = [s["outer_iters"] for s in stats]
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": config_json(cfg), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk, "dslash": dsl, "plain_fp64": plain,
+        "solver": {"gcr_iters_sloppy": [min(iters[:12 * WORKLOAD["n_g"]]), max(iters[:12 * WORKLOAD["n_g"]])],
+                   "gcr_iters_exact": [min(iters[12 * WORKLOAD["n_g"]:]), max(iters[12 * WORKLOAD["n_g"]:])],
+                   "max_true_residual_exact": max(s["true_rel_residual"] for s in stats[12 * WORKLOAD["n_g"]:]),
+                   "kernel_ms": {k: round(v["ms"] / args.steps, 1) for k, v in prof.items()}},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    lat.close()
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, _ = workload_config()
+    vals = []
+    desc, thr = "", 1
+    budget = max(5.0, args.cpu_budget / 2)
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; each step is an independent bounded sample
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, desc, thr = oracle_sample(budget)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": config_json(cfg),
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -74,6 +74,10 @@ typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
  *               and Krylov basis (mixed precision, Sec. 2.2 last paragraph);
  *               QCD_PREC_F64: everything in FP64.
  *   rhs_tile    right-hand sides solved together (0 = library choice).
+ *   sap_half    FP32 SAP only: 1 = the block's links and clover term are held
+ *               as 16-bit copies in shared memory during a block solve (the
+ *               preconditioner changes by their rounding; the outer flexible
+ *               GCR is unaffected in what it converges to); 0 = FP32 copies.
  */
 typedef struct {
   int block[4];
@@ -84,6 +88,7 @@ typedef struct {
   double restart_drop;
   int precision;
   int rhs_tile;
+  int sap_half;
 } qcd_solver_params;
 
 /* Per right-hand-side outcome of a solve. */
@@ -113,7 +118,7 @@ qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int U_on_device, double
                           int time_bc);
 
 /* Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
- * restart_drop 1e-5, precision F32, rhs_tile 0. */
+ * restart_drop 1e-5, precision F32, rhs_tile 0, sap_half 0. */
 void qcd_default_params(qcd_solver_params* p);
 qcd_status qcd_set_params(qcd_ctx* ctx, const qcd_solver_params* p);
 

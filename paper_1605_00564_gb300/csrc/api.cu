@@ -53,10 +53,11 @@ void devbuf_free(DevBuf& b) {
   b.bytes = 0;
 }
 
-ProfScope::ProfScope(qcd_ctx* c_, int fam, double bytes, double flops) : c(c_), idx(-1) {
+ProfScope::ProfScope(qcd_ctx* c_, int fam, double bytes, double flops, int kernels) : c(c_), idx(-1) {
   if (!c || !c->prof_on) return;
   ProfRec r;
   r.fam = fam;
+  r.kernels = kernels;
   r.bytes = bytes;
   r.flops = flops;
   for (cudaEvent_t* e : {&r.a, &r.b}) {
@@ -114,6 +115,7 @@ qcd_status validate_params(const qcd_ctx* c, const qcd_solver_params* p) {
   ARG_CHECK(p->restart_drop >= 0 && p->restart_drop < 1, "restart_drop must be in [0, 1)");
   ARG_CHECK(p->precision == QCD_PREC_F64 || p->precision == QCD_PREC_F32, "unknown precision %d", p->precision);
   ARG_CHECK(p->rhs_tile >= 0, "rhs_tile must be >= 0");
+  ARG_CHECK(p->sap_half == 0 || p->sap_half == 1, "sap_half must be 0 or 1");
   return QCD_OK;
 }
 
@@ -152,6 +154,7 @@ void qcd_default_params(qcd_solver_params* p) {
   p->restart_drop = 1e-5;
   p->precision = QCD_PREC_F32;
   p->rhs_tile = 0;
+  p->sap_half = 0;
 }
 
 qcd_status qcd_create(qcd_ctx** out, const int dims[4], void* cuda_stream) {
@@ -372,7 +375,10 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* c, const int* src, int n_src, int n_exac
       qcd_set_error("source set-up failed");
       break;
     }
-    k_point_sources<<<(n + 63) / 64, 64, 0, c->stream>>>((double2*)c->wsD[0].p, d_sites, c->g.V, n);
+    {
+      ProfScope ps(c, FAM_LAYOUT, 0.0, 0.0);
+      k_point_sources<<<(n + 63) / 64, 64, 0, c->stream>>>((double2*)c->wsD[0].p, d_sites, c->g.V, n);
+    }
     rc = solver_run(c, n, tols.data(), st.data() + (size_t)12 * j0);
     if (rc != QCD_OK) break;
     for (int k = 0; k < nj && rc == QCD_OK; k++) {
@@ -427,7 +433,7 @@ qcd_status qcd_profile_read(qcd_ctx* c, qcd_kernel_time* out, int max, int* n) {
   for (auto& r : c->prof) {
     float ms = 0;
     QCD_CUDA_OK(cudaEventElapsedTime(&ms, r.a, r.b));
-    acc[r.fam].launches++;
+    acc[r.fam].launches += r.kernels;
     acc[r.fam].ms += ms;
     acc[r.fam].bytes += r.bytes;
     acc[r.fam].flops += r.flops;

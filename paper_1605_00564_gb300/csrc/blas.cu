@@ -133,7 +133,7 @@ template <typename X, typename Y, int OP>
 qcd_status reduce(qcd_ctx* c, const void* x, const void* y, int nrhs, void* out, const int* mask) {
   int G = red_grid(c);
   QCD_TRY(devbuf_ensure(c->red, (size_t)G * nrhs * sizeof(double2)));
-  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nrhs * (X::bytes + (OP ? Y::bytes : 0)), (double)c->g.V * nrhs * 96);
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nrhs * (X::bytes + (OP ? Y::bytes : 0)), (double)c->g.V * nrhs * 96, 2);
   k_reduce<X, Y, OP><<<dim3(G, nrhs), RED_TPB, 0, c->stream>>>((const char*)x, (const char*)y, c->g.V,
                                                                 (double2*)c->red.p, mask);
   k_reduce_final<<<nrhs, RED_TPB, 0, c->stream>>>((const double2*)c->red.p, G, (double2*)out, OP, mask);
@@ -245,6 +245,164 @@ __global__ void k_convert(const char* __restrict__ in, char* __restrict__ out, i
 }
 
 inline dim3 grid2(const qcd_ctx* c, int nrhs) { return dim3((c->g.V + 255) / 256, nrhs); }
+// ---------------------------------------------------------------------------
+// Fused Gram-Schmidt step of the GCR solver
+// ---------------------------------------------------------------------------
+constexpr int GS_TPB = 256;
+
+// block sum of NV doubles; thread 0 holds the result in out[]
+template <int NV>
+__device__ inline void block_sum_n(double (&v)[NV], double* sh /* [NV][32] */) {
+#pragma unroll
+  for (int k = 0; k < NV; k++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < NV; k++) sh[k * 32 + w] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      double t = 0;
+      for (int ww = 0; ww < nw; ww++) t += sh[k * 32 + ww];
+      v[k] = t;
+    }
+}
+
+// dots[j][r] = (chi_j, chi_k) for j < k: chi_k is read once, each chi_j once.
+// One thread per site; per-j CTA sums go to part[r][j][cta].
+template <typename X>
+__global__ void __launch_bounds__(GS_TPB) k_multi_dot(const char* __restrict__ chi, size_t jstride, int k, int V,
+                                                       double2* __restrict__ part, const int* mask) {
+  __shared__ double sh[2 * 32];
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t roff = (size_t)rhs * X::bytes * V;
+  using R = typename X::R;
+  Cplx<R> ck[12];
+  if (s < V) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) X::ld(chi + k * jstride + roff, V, q, s, ck[2 * q], ck[2 * q + 1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 12; q++) ck[q] = cmk((R)0, (R)0);
+  }
+  for (int j = 0; j < k; j++) {
+    R sr = 0, si = 0;
+    if (s < V) {
+#pragma unroll
+      for (int q = 0; q < 6; q++) {
+        Cplx<R> a, b;
+        X::ld(chi + j * jstride + roff, V, q, s, a, b);
+        sr += a.re * ck[2 * q].re + a.im * ck[2 * q].im + b.re * ck[2 * q + 1].re + b.im * ck[2 * q + 1].im;
+        si += a.re * ck[2 * q].im - a.im * ck[2 * q].re + b.re * ck[2 * q + 1].im - b.im * ck[2 * q + 1].re;
+      }
+    }
+    double v[2] = {(double)sr, (double)si};
+    block_sum_n<2>(v, sh);
+    if (threadIdx.x == 0) part[((size_t)rhs * k + j) * gridDim.x + blockIdx.x] = make_double2(v[0], v[1]);
+  }
+}
+
+// out[j*nrhs + r] = sum over g of part[r][j][g] (fixed order)
+__global__ void __launch_bounds__(RED_TPB) k_sum_parts(const double2* __restrict__ part, int nj, int G,
+                                                       double2* __restrict__ out, int nrhs, const int* mask) {
+  const int j = blockIdx.x, rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  double2 acc = make_double2(0, 0);
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    double2 v = part[((size_t)rhs * nj + j) * G + i];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  double2 t = block_sum(acc);
+  if (threadIdx.x == 0) out[(size_t)j * nrhs + rhs] = t;
+}
+
+// chi_k -= sum_{j<k} dots[j] chi_j; then partial sums of |chi_k|^2 and (chi_k, rho)
+template <typename X>
+__global__ void __launch_bounds__(GS_TPB) k_gs_orth(char* __restrict__ chi, size_t jstride, int k,
+                                                     const double2* __restrict__ dots, const char* __restrict__ rho,
+                                                     int V, int nrhs, double2* __restrict__ part, const int* mask) {
+  __shared__ double sh[3 * 32];
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  using R = typename X::R;
+  const size_t roff = (size_t)rhs * X::bytes * V;
+  char* ckp = chi + k * jstride + roff;
+  const char* rp = rho + (size_t)rhs * PD::bytes * V;
+  double n2 = 0, cr = 0, ci = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+#pragma unroll 1
+    for (int q = 0; q < 6; q++) {
+      Cplx<R> a, b;
+      X::ld(ckp, V, q, s, a, b);
+      for (int j = 0; j < k; j++) {
+        double2 d = dots[(size_t)j * nrhs + rhs];
+        Cplx<R> w = cmk((R)d.x, (R)d.y), u, v;
+        X::ld(chi + j * jstride + roff, V, q, s, u, v);
+        a = a - w * u;
+        b = b - w * v;
+      }
+      X::st(ckp, V, q, s, a, b);
+      Cplx<double> x, y;
+      PD::ld(rp, V, q, s, x, y);
+      n2 += (double)(a.re * a.re + a.im * a.im + b.re * b.re + b.im * b.im);
+      cr += (double)a.re * x.re + (double)a.im * x.im + (double)b.re * y.re + (double)b.im * y.im;
+      ci += (double)a.re * x.im - (double)a.im * x.re + (double)b.re * y.im - (double)b.im * y.re;
+    }
+  }
+  double v[3] = {n2, cr, ci};
+  block_sum_n<3>(v, sh);
+  if (threadIdx.x == 0) {
+    double2* p = part + (size_t)rhs * 2 * gridDim.x;
+    p[blockIdx.x] = make_double2(v[0], 0.0);
+    p[gridDim.x + blockIdx.x] = make_double2(v[1], v[2]);
+  }
+}
+
+// chi_k *= inv; rho -= ck * chi_k; rho_s = rho in the inner precision; partial |rho|^2
+template <typename X>
+__global__ void __launch_bounds__(GS_TPB) k_gs_finish(char* __restrict__ chik, const double* __restrict__ inv,
+                                                       const double2* __restrict__ ck, char* __restrict__ rho,
+                                                       char* __restrict__ rho_s, int V, double2* __restrict__ part,
+                                                       const int* mask) {
+  __shared__ double sh[32];
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  using R = typename X::R;
+  char* cp = chik + (size_t)rhs * X::bytes * V;
+  char* rp = rho + (size_t)rhs * PD::bytes * V;
+  char* sp = rho_s + (size_t)rhs * X::bytes * V;
+  const R f = (R)inv[rhs];
+  const Cplx<double> c = cmk(ck[rhs].x, ck[rhs].y);
+  double n2 = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      Cplx<R> a, b;
+      X::ld(cp, V, q, s, a, b);
+      a = f * a;
+      b = f * b;
+      X::st(cp, V, q, s, a, b);
+      Cplx<double> x, y;
+      PD::ld(rp, V, q, s, x, y);
+      x = x - c * cmk((double)a.re, (double)a.im);
+      y = y - c * cmk((double)b.re, (double)b.im);
+      PD::st(rp, V, q, s, x, y);
+      X::st(sp, V, q, s, cmk((R)x.re, (R)x.im), cmk((R)y.re, (R)y.im));
+      n2 += x.re * x.re + x.im * x.im + y.re * y.re + y.im * y.im;
+    }
+  }
+  double v[1] = {n2};
+  block_sum_n<1>(v, sh);
+  if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = make_double2(v[0], 0.0);
+}
+
 
 }  // namespace
 
@@ -317,6 +475,67 @@ qcd_status blas_convert(qcd_ctx* c, const void* in, int pin, void* out, int pout
     k_convert<PD, PD><<<g, 256, 0, c->stream>>>((const char*)in, (char*)out, c->g.V, nrhs, mask);
   else
     k_convert<PF, PF><<<g, 256, 0, c->stream>>>((const char*)in, (char*)out, c->g.V, nrhs, mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+// dots_dev[j][r] = (chi_j, chi_k), j < k
+qcd_status blas_gs_dots(qcd_ctx* c, const void* chi, int prec, size_t jstride, int k, int nrhs, double* dots_dev,
+                        const int* mask, int nactive) {
+  if (k <= 0) return QCD_OK;
+  const int G = (c->g.V + GS_TPB - 1) / GS_TPB;
+  QCD_TRY(devbuf_ensure(c->red, (size_t)G * k * nrhs * sizeof(double2)));
+  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * (k + 1) * vb, (double)c->g.V * nactive * k * 48, 2);
+  if (prec == QCD_PREC_F64)
+    k_multi_dot<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((const char*)chi, jstride, k, c->g.V,
+                                                            (double2*)c->red.p, mask);
+  else
+    k_multi_dot<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((const char*)chi, jstride, k, c->g.V,
+                                                            (double2*)c->red.p, mask);
+  k_sum_parts<<<dim3(k, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, k, G, (double2*)dots_dev, nrhs,
+                                                        mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+// chi_k -= sum_j dots[j] chi_j; n2c[0][r] = |chi_k|^2 (re), n2c[1][r] = (chi_k, rho)
+qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, const double* dots_dev,
+                        const void* rho, int nrhs, double* n2c_dev, const int* mask, int nactive) {
+  const int G = red_grid(c);
+  QCD_TRY(devbuf_ensure(c->red, (size_t)G * 2 * nrhs * sizeof(double2)));
+  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * ((k + 2) * vb + 192), (double)c->g.V * nactive * (k + 2) * 48,
+               2);
+  if (prec == QCD_PREC_F64)
+    k_gs_orth<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chi, jstride, k, (const double2*)dots_dev,
+                                                          (const char*)rho, c->g.V, nrhs, (double2*)c->red.p, mask);
+  else
+    k_gs_orth<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chi, jstride, k, (const double2*)dots_dev,
+                                                          (const char*)rho, c->g.V, nrhs, (double2*)c->red.p, mask);
+  k_sum_parts<<<dim3(2, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 2, G, (double2*)n2c_dev, nrhs,
+                                                        mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+// chi_k *= inv; rho -= ck chi_k; rho_s = (inner precision) rho; rn2[r] = |rho|^2 (as double2 .x)
+qcd_status blas_gs_finish(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev, void* rho,
+                          void* rho_s, int nrhs, double* rn2_dev, const int* mask, int nactive) {
+  const int G = red_grid(c);
+  QCD_TRY(devbuf_ensure(c->red, (size_t)G * nrhs * sizeof(double2)));
+  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * (3 * vb + 2 * 192), (double)c->g.V * nactive * 96, 2);
+  if (prec == QCD_PREC_F64)
+    k_gs_finish<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
+                                                            (char*)rho, (char*)rho_s, c->g.V, (double2*)c->red.p,
+                                                            mask);
+  else
+    k_gs_finish<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
+                                                            (char*)rho, (char*)rho_s, c->g.V, (double2*)c->red.p,
+                                                            mask);
+  k_sum_parts<<<dim3(1, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 1, G, (double2*)rn2_dev, nrhs,
+                                                        mask);
   QCD_CUDA_OK(cudaGetLastError());
   return QCD_OK;
 }

@@ -168,7 +168,7 @@ qcd_status contract_nucleon(qcd_ctx* c, const void* prop, int t0, double* corr_d
   const int bc3 = c->g.bc_t * c->g.bc_t * c->g.bc_t;
   // algorithmic cost per site: the 144 complex propagator entries read once;
   // 36 colour-permutation pairs x (16 + 64 + 32) complex multiply-adds
-  ProfScope ps(c, FAM_CONTRACT, (double)c->g.V * 144 * 16, (double)c->g.V * 36 * 112 * 8);
+  ProfScope ps(c, FAM_CONTRACT, (double)c->g.V * 144 * 16, (double)c->g.V * 36 * 112 * 8, 2);
   if (precision == QCD_PREC_F64) {
     size_t smem = (size_t)144 * ns * sizeof(Cplx<double>);
     QCD_CUDA_OK(cudaFuncSetAttribute(k_nucleon<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -315,7 +315,7 @@ void devbuf_free(DevBuf& b);
 enum ProfFam { FAM_DSLASH_D, FAM_DSLASH_F, FAM_SAP_D, FAM_SAP_F, FAM_BLAS, FAM_LAYOUT, FAM_CONTRACT, FAM_N };
 
 struct ProfRec {
-  int fam;
+  int fam, kernels;
   cudaEvent_t a, b;
   double bytes, flops;
 };
@@ -350,7 +350,7 @@ struct qcd_ctx {
 struct ProfScope {
   qcd_ctx* c;
   int idx;
-  ProfScope(qcd_ctx* c, int fam, double bytes, double flops);
+  ProfScope(qcd_ctx* c, int fam, double bytes, double flops, int kernels = 1);
   ~ProfScope();
 };
 
@@ -378,6 +378,13 @@ qcd_status blas_convert(qcd_ctx* c, const void* in, int pin, void* out, int pout
 qcd_status blas_multi_caxpy(qcd_ctx* c, void* y, int py, const void* xbase, int px, int nx, size_t xstride,
                             const double* coef_dev, double sign, int nrhs, const int* mask);
 qcd_status blas_scale(qcd_ctx* c, void* x, int px, const double* sc_dev, int nrhs, const int* mask);
+// fused Gram-Schmidt step of the GCR cycle (chi_j at chi + j*jstride bytes, j <= k)
+qcd_status blas_gs_dots(qcd_ctx* c, const void* chi, int prec, size_t jstride, int k, int nrhs, double* dots_dev,
+                        const int* mask, int nactive);
+qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, const double* dots_dev,
+                        const void* rho, int nrhs, double* n2c_dev, const int* mask, int nactive);
+qcd_status blas_gs_finish(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev, void* rho,
+                          void* rho_s, int nrhs, double* rn2_dev, const int* mask, int nactive);
 // out = x - y
 qcd_status blas_xmy(qcd_ctx* c, const void* x, const void* y, void* out, int prec, int nrhs, const int* mask);
 

@@ -20,6 +20,8 @@
 // One CTA per block and right-hand side, one thread per block site; the
 // block's residual lives in shared memory across the MR steps, the solution
 // increment x in registers.
+#include <cuda_fp16.h>
+
 #include "qcd_internal.cuh"
 
 namespace {
@@ -200,6 +202,202 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(char* __restrict__ rho
   F::store_spinor(delta, g.V, s, x);
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory-resident variant (FP32 arithmetic).  The block's links (two
+// rows each) and clover term are staged in shared memory once per sweep, so
+// the n_mr MR steps read only shared memory.  S selects the storage of the
+// staged copies: float (exact single precision) or __half (16-bit copies of
+// links and clover, half the shared memory, two CTAs per SM; the
+// preconditioner is then a slightly different operator, which the flexible
+// outer GCR tolerates).
+// ---------------------------------------------------------------------------
+template <typename S>
+struct Stage;
+template <>
+struct Stage<float> {
+  using W = float4;
+  static __device__ inline W put(float4 v) { return v; }
+  static __device__ inline float4 get(W w) { return w; }
+};
+template <>
+struct Stage<__half> {
+  using W = uint2;
+  static __device__ inline W put(float4 v) {
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    W w;
+    w.x = *reinterpret_cast<unsigned*>(&a);
+    w.y = *reinterpret_cast<unsigned*>(&b);
+    return w;
+  }
+  static __device__ inline float4 get(W w) {
+    float2 a = __half22float2(*reinterpret_cast<__half2*>(&w.x));
+    float2 b = __half22float2(*reinterpret_cast<__half2*>(&w.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+};
+
+template <typename S>
+__device__ inline SU3<float> smem_link(const typename Stage<S>::W* lk, int vb, int mu, int l) {
+  const typename Stage<S>::W* p = lk + (size_t)mu * 3 * vb;
+  float4 a = Stage<S>::get(p[l]), b = Stage<S>::get(p[vb + l]), c = Stage<S>::get(p[2 * vb + l]);
+  SU3<float> U;
+  U.m[0][0] = cmk(a.x, a.y); U.m[0][1] = cmk(a.z, a.w); U.m[0][2] = cmk(b.x, b.y);
+  U.m[1][0] = cmk(b.z, b.w); U.m[1][1] = cmk(c.x, c.y); U.m[1][2] = cmk(c.z, c.w);
+  U.m[2][0] = conj(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
+  U.m[2][1] = conj(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
+  U.m[2][2] = conj(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
+  return U;
+}
+
+template <typename S>
+__device__ inline Spinor<float> smem_clover_apply(const typename Stage<S>::W* cl, int vb, int l,
+                                                  const Spinor<float>& p) {
+  Spinor<float> o;
+#pragma unroll
+  for (int b = 0; b < 2; b++) {
+    float c[36];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      float4 v = Stage<S>::get(cl[(size_t)(9 * b + k) * vb + l]);
+      c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+    }
+    clover_block_apply(c, 0, &p.c[6 * b], &o.c[6 * b]);
+  }
+  return o;
+}
+
+template <typename S, int MU>
+__device__ inline void smem_block_hop(Spinor<float>& p, const Cplx<float>* r_s, const typename Stage<S>::W* lk,
+                                      const SapGeom& sg, int l, const int lc[4], float scale) {
+  if (lc[MU] < sg.b[MU] - 1) {
+    HalfSpinor<float> h = project<MU, -1>(smem_load(r_s, sg.vb, l + sg.lst[MU]));
+    h = su3_mul(smem_link<S>(lk, sg.vb, MU, l), h);
+    accum_recon<MU, -1>(p, h, scale);
+  }
+  if (lc[MU] > 0) {
+    HalfSpinor<float> h = project<MU, +1>(smem_load(r_s, sg.vb, l - sg.lst[MU]));
+    h = su3_dag_mul(smem_link<S>(lk, sg.vb, MU, l - sg.lst[MU]), h);
+    accum_recon<MU, +1>(p, h, scale);
+  }
+}
+
+template <typename S, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+    k_sap_sweep_smem(char* __restrict__ rho, char* __restrict__ psi, char* __restrict__ delta,
+                     const float4* __restrict__ gauge, const float4* __restrict__ clover, Geom g, SapGeom sg,
+                     int colour, int gather, int psi_init, float kappa, int nmr, int nrhs, const int* mask) {
+  using W = typename Stage<S>::W;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int vb = sg.vb;
+  Cplx<float>* r_s = (Cplx<float>*)smem_raw;
+  W* lk_s = (W*)(smem_raw + (size_t)12 * vb * sizeof(Cplx<float>));
+  W* cl_s = lk_s + (size_t)12 * vb;
+  __shared__ float red[3][32];
+
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  const size_t off = (size_t)rhs * FieldsF::spinor_bytes * g.V;
+  rho += off;
+  psi += off;
+  delta += off;
+
+  const int nbx2 = sg.nb[1] >> 1;
+  int q = blockIdx.x / nbx2;
+  const int j = blockIdx.x - q * nbx2;
+  const int by = q % sg.nb[2];
+  q /= sg.nb[2];
+  const int bz = q % sg.nb[3];
+  const int bt = q / sg.nb[3];
+  const int bx = 2 * j + ((colour + bt + bz + by) & 1);
+
+  const int l = threadIdx.x;
+  int lc[4], c[4];
+  {
+    int r = l;
+    lc[1] = r % sg.b[1]; r /= sg.b[1];
+    lc[2] = r % sg.b[2]; r /= sg.b[2];
+    lc[3] = r % sg.b[3];
+    lc[0] = r / sg.b[3];
+  }
+  c[0] = bt * sg.b[0] + lc[0];
+  c[1] = bx * sg.b[1] + lc[1];
+  c[2] = by * sg.b[2] + lc[2];
+  c[3] = bz * sg.b[3] + lc[3];
+  const int s = ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
+
+  // stage this site's four links (rows 0, 1) and its clover term
+#pragma unroll
+  for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) lk_s[(size_t)(3 * mu + k) * vb + l] = Stage<S>::put(__ldg(gauge + (size_t)(3 * mu + k) * g.V + s));
+#pragma unroll
+  for (int k = 0; k < 18; k++) cl_s[(size_t)k * vb + l] = Stage<S>::put(__ldg(clover + (size_t)k * g.V + s));
+
+  Spinor<float> r = FieldsF::load_spinor(rho, g.V, s);
+  if (gather) {
+    face_hop<FieldsF, 0>(r, delta, sg, gauge, g, s, c, lc, kappa);
+    face_hop<FieldsF, 1>(r, delta, sg, gauge, g, s, c, lc, kappa);
+    face_hop<FieldsF, 2>(r, delta, sg, gauge, g, s, c, lc, kappa);
+    face_hop<FieldsF, 3>(r, delta, sg, gauge, g, s, c, lc, kappa);
+  }
+  smem_store(r_s, vb, l, r);
+
+  Spinor<float> x;
+#pragma unroll
+  for (int k = 0; k < 12; k++) x.c[k] = cmk(0.f, 0.f);
+
+  const int warp = l >> 5, lane = l & 31, nw = (vb + 31) >> 5;
+  for (int step = 0; step < nmr; step++) {
+    __syncthreads();
+    Spinor<float> p = smem_clover_apply<S>(cl_s, vb, l, r);
+    smem_block_hop<S, 0>(p, r_s, lk_s, sg, l, lc, -kappa);
+    smem_block_hop<S, 1>(p, r_s, lk_s, sg, l, lc, -kappa);
+    smem_block_hop<S, 2>(p, r_s, lk_s, sg, l, lc, -kappa);
+    smem_block_hop<S, 3>(p, r_s, lk_s, sg, l, lc, -kappa);
+    float pr_re = 0, pr_im = 0, pp = 0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      pr_re += p.c[k].re * r.c[k].re + p.c[k].im * r.c[k].im;
+      pr_im += p.c[k].re * r.c[k].im - p.c[k].im * r.c[k].re;
+      pp += p.c[k].re * p.c[k].re + p.c[k].im * p.c[k].im;
+    }
+    pr_re = warp_sum(pr_re);
+    pr_im = warp_sum(pr_im);
+    pp = warp_sum(pp);
+    if (lane == 0) {
+      red[0][warp] = pr_re;
+      red[1][warp] = pr_im;
+      red[2][warp] = pp;
+    }
+    __syncthreads();
+    float a_re = 0, a_im = 0, n2 = 0;
+    for (int w = 0; w < nw; w++) {
+      a_re += red[0][w];
+      a_im += red[1][w];
+      n2 += red[2][w];
+    }
+    Cplx<float> alpha = n2 > 0.f ? cmk(a_re / n2, a_im / n2) : cmk(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      x.c[k] = x.c[k] + alpha * r.c[k];
+      r.c[k] = r.c[k] - alpha * p.c[k];
+    }
+    __syncthreads();
+    smem_store(r_s, vb, l, r);
+  }
+
+  if (psi_init) {
+    FieldsF::store_spinor(psi, g.V, s, x);
+  } else {
+    Spinor<float> y = FieldsF::load_spinor(psi, g.V, s);
+#pragma unroll
+    for (int k = 0; k < 12; k++) y.c[k] = y.c[k] + x.c[k];
+    FieldsF::store_spinor(psi, g.V, s, y);
+  }
+  FieldsF::store_spinor(rho, g.V, s, r);
+  FieldsF::store_spinor(delta, g.V, s, x);
+}
+
 template <typename F>
 qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const void* gauge, const void* clover,
                          int nrhs, const int* mask, int nactive) {
@@ -237,12 +435,23 @@ qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const vo
   const double half = c->g.V / 2.0;
   const double flops_site = P.nmr * (1320.0 * (1.0 - face / 8.0) + 504.0 + 192.0) + 165.0 * face;
   const int fam = sizeof(typename F::R) == 8 ? FAM_SAP_D : FAM_SAP_F;
+  // FP32 with blocks of at most 256 sites: the shared-memory-resident kernel
+  const bool resident = sizeof(typename F::R) == 4 && sg.vb <= 256;
+  auto kres = P.sap_half ? k_sap_sweep_smem<__half, 256, 2> : k_sap_sweep_smem<float, 256, 1>;
+  const size_t smem_res = (size_t)sg.vb * (96 + (P.sap_half ? 96 + 144 : 192 + 288));
+  if (resident)
+    QCD_CUDA_OK(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res));
   for (int cy = 0; cy < P.ncy; cy++)
     for (int col = 0; col < 2; col++) {
       const double bytes_site = sb * (2 + (cy == 0 ? 1 : 2) + 1 + face) + 4 * lb + cb;
       ProfScope ps(c, fam, half * nactive * bytes_site, half * nactive * flops_site);
-      kern<<<grid, sg.vb, smem, c->stream>>>(rho, psi, delta, gauge, clover, c->g, sg, col, !(cy == 0 && col == 0),
-                                             cy == 0, (typename F::R)c->kappa, P.nmr, nrhs, mask);
+      if (resident)
+        kres<<<grid, sg.vb, smem_res, c->stream>>>(rho, psi, delta, (const float4*)gauge, (const float4*)clover, c->g,
+                                                   sg, col, !(cy == 0 && col == 0), cy == 0, (float)c->kappa, P.nmr,
+                                                   nrhs, mask);
+      else
+        kern<<<grid, sg.vb, smem, c->stream>>>(rho, psi, delta, gauge, clover, c->g, sg, col, !(cy == 0 && col == 0),
+                                               cy == 0, (typename F::R)c->kappa, P.nmr, nrhs, mask);
       QCD_CUDA_OK(cudaGetLastError());
     }
   return QCD_OK;

@@ -28,12 +28,15 @@
 
 namespace {
 
-__global__ void k_gs_norm(const double* nrm, double* b, double* inv, int n, const int* mask) {
+// b = |chi_k|, inv = 1/b, c_k = (chi_k, rho) / b from n2c = {|chi_k|^2, (chi_k, rho)}
+__global__ void k_gs_scalars(const double2* n2c, double* b, double* inv, double2* ck, int n, const int* mask) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n || (mask && !mask[r])) return;
-  double v = sqrt(nrm[r]);
+  double v = sqrt(n2c[r].x);
+  double iv = v > 0 ? 1.0 / v : 0.0;
   b[r] = v;
-  inv[r] = v > 0 ? 1.0 / v : 0.0;
+  inv[r] = iv;
+  ck[r] = make_double2(n2c[n + r].x * iv, n2c[n + r].y * iv);
 }
 
 struct Work {
@@ -41,7 +44,8 @@ struct Work {
   char *rhoS, *delta;               // inner precision [n]
   char *phi, *chi;                  // inner precision [nkv][n]
   double2 *a;                       // [nkv][nkv][n]: a[k][j][r]
-  double *b, *inv, *nrm, *rn2;      // [nkv][n], [n], [n], [n]
+  double *b, *inv, *rn2;            // [nkv][n], [n], [n]
+  double2 *n2c, *rn2c;              // [2][n], [n]
   double2 *cc, *alpha;              // [nkv][n]
   int* mask;                        // [n]
 };
@@ -67,14 +71,15 @@ qcd_status get_work(qcd_ctx* c, int n, int nkv, int prec, Work& w) {
   w.phi = w.delta + VI;
   w.chi = w.phi + VI * nkv;
   size_t sz = align256(sizeof(double2) * nkv * nkv * n) + align256(sizeof(double) * nkv * n) +
-              3 * align256(sizeof(double) * n) + 2 * align256(sizeof(double2) * nkv * n) + align256(sizeof(int) * n);
+              2 * align256(sizeof(double) * n) + 2 * align256(sizeof(double2) * nkv * n) +
+              align256(sizeof(double2) * 3 * n) + align256(sizeof(int) * n);
   QCD_TRY(devbuf_ensure(c->scal, sz));
   char* p = (char*)c->scal.p;
   w.a = (double2*)p;  p += align256(sizeof(double2) * nkv * nkv * n);
   w.b = (double*)p;   p += align256(sizeof(double) * nkv * n);
   w.inv = (double*)p; p += align256(sizeof(double) * n);
-  w.nrm = (double*)p; p += align256(sizeof(double) * n);
   w.rn2 = (double*)p; p += align256(sizeof(double) * n);
+  w.n2c = (double2*)p; w.rn2c = w.n2c + 2 * n; p += align256(sizeof(double2) * 3 * n);
   w.cc = (double2*)p; p += align256(sizeof(double2) * nkv * n);
   w.alpha = (double2*)p; p += align256(sizeof(double2) * nkv * n);
   w.mask = (int*)p;
@@ -111,7 +116,8 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
   QCD_TRY(host_mirror(c, sizeof(double) * (8 * n + nkv * nkv * n * 2 + 4 * nkv * n * 2) + 64));
   double* h_rn2 = c->host_scal;
   double* h_eta = h_rn2 + n;
-  double2* h_a = (double2*)(h_eta + n);
+  double2* h_rn2c = (double2*)(h_eta + n);
+  double2* h_a = h_rn2c + n;
   double* h_b = (double*)(h_a + (size_t)nkv * nkv * n);
   double2* h_c = (double2*)(h_b + (size_t)nkv * n);
   double2* h_alpha = h_c + (size_t)nkv * n;
@@ -194,22 +200,24 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
       for (int r = 0; r < n; r++) nin_now += incyc[r];
       char* phik = w.phi + VI * k;
       char* chik = w.chi + VI * k;
-      QCD_TRY(blas_convert(c, w.rho, QCD_PREC_F64, w.rhoS, prec, n, w.mask));
+      if (k == 0) QCD_TRY(blas_convert(c, w.rho, QCD_PREC_F64, w.rhoS, prec, n, w.mask));
       QCD_TRY(sap_apply(c, w.rhoS, phik, w.delta, prec, n, w.mask, nin_now));
       QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now));
+      // Gram-Schmidt against chi_0..chi_{k-1}, normalisation, residual update;
+      // the update also writes the next preconditioner input rhoS
       double2* ak = w.a + (size_t)k * nkv * n;
-      for (int j = 0; j < k; j++)
-        QCD_TRY(blas_dot(c, w.chi + VI * j, prec, chik, prec, n, (double*)(ak + (size_t)j * n), w.mask));
-      QCD_TRY(blas_multi_caxpy(c, chik, prec, w.chi, prec, k, VI, (const double*)ak, -1.0, n, w.mask));
-      QCD_TRY(blas_norm2(c, chik, prec, n, w.nrm, w.mask));
-      k_gs_norm<<<(n + 63) / 64, 64, 0, c->stream>>>(w.nrm, w.b + (size_t)k * n, w.inv, n, w.mask);
+      QCD_TRY(blas_gs_dots(c, w.chi, prec, VI, k, n, (double*)ak, w.mask, nin_now));
+      QCD_TRY(blas_gs_orth(c, w.chi, prec, VI, k, (const double*)ak, w.rho, n, (double*)w.n2c, w.mask, nin_now));
+      {
+        ProfScope ps(c, FAM_BLAS, 0.0, 0.0);
+        k_gs_scalars<<<(n + 63) / 64, 64, 0, c->stream>>>(w.n2c, w.b + (size_t)k * n, w.inv, w.cc + (size_t)k * n, n,
+                                                          w.mask);
+      }
       QCD_CUDA_OK(cudaGetLastError());
-      QCD_TRY(blas_scale(c, chik, prec, w.inv, n, w.mask));
-      QCD_TRY(blas_dot(c, chik, prec, w.rho, QCD_PREC_F64, n, (double*)(w.cc + (size_t)k * n), w.mask));
-      QCD_TRY(blas_multi_caxpy(c, w.rho, QCD_PREC_F64, chik, prec, 1, VI, (const double*)(w.cc + (size_t)k * n),
-                               -1.0, n, w.mask));
-      QCD_TRY(blas_norm2(c, w.rho, QCD_PREC_F64, n, w.rn2, w.mask));
-      QCD_TRY(fetch(c, h_rn2, w.rn2, sizeof(double) * n));
+      QCD_TRY(blas_gs_finish(c, chik, prec, w.inv, (const double*)(w.cc + (size_t)k * n), w.rho, w.rhoS, n,
+                             (double*)w.rn2c, w.mask, nin_now));
+      QCD_TRY(fetch(c, h_rn2c, w.rn2c, sizeof(double2) * n));
+      for (int r = 0; r < n; r++) h_rn2[r] = h_rn2c[r].x;
       kmax = k + 1;
       int nin = 0;
       for (int r = 0; r < n; r++) {

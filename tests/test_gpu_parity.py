@@ -6,6 +6,7 @@ Tolerances (norm-wise relative unless stated):
   clover term, FP64    1e-14   (max abs)
   SAP FP64 vs oracle   1e-11   (identical MR algorithm in FP64)
   SAP FP32 vs oracle   2e-4    (MR step lengths in FP32)
+  SAP FP32, 16-bit block copies of links/clover: 5e-3 (rounding of the copies)
   exact solve          oracle-computed residual <= 1.1e-10, solution <= 1e-8
   sloppy solve         oracle-computed residual <= 1e-3
   contraction FP64     1e-12 of max |C|; FP32 2e-5 of max |C|
@@ -65,12 +66,12 @@ def test_clover_field(small):
     assert np.abs(ref[..., :6, 6:]).max() == 0.0
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 2e-4)])
+@pytest.mark.parametrize("prec,half,tol", [("f64", 0, 1e-11), ("f32", 0, 2e-4), ("f32", 1, 5e-3)])
 @pytest.mark.parametrize("block", [(4, 4, 4, 4), (8, 4, 4, 4), (4, 2, 4, 2)])
-def test_sap_matches_oracle(small, prec, tol, block):
+def test_sap_matches_oracle(small, prec, half, tol, block):
     from oracle.sap import SAP
     lat, op, _ = small
-    lat.set_params(block=block, ncy=3, nmr=4)
+    lat.set_params(block=block, ncy=3, nmr=4, sap_half=half)
     eta = synth.random_spinor(lat.dims, 11, nrhs=2)
     out = to_host(lat.apply_sap(to_dev(eta), precision=prec))
     s = SAP(op, block, ncy=3, nmr=4)
@@ -78,10 +79,11 @@ def test_sap_matches_oracle(small, prec, tol, block):
     assert rel(out, ref) < tol
 
 
-def test_solve_exact_and_sloppy(small):
+@pytest.mark.parametrize("half", [0, 1])
+def test_solve_exact_and_sloppy(small, half):
     from oracle.solve import gcr
     lat, op, _ = small
-    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32")
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=half)
     src = synth.point_sources(lat.dims, (0, 0, 0, 0))
     eta = to_dev(src)
     psi, st = lat.solve(eta, 1e-10)
