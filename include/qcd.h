@@ -74,6 +74,15 @@ typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
  *               and Krylov basis (mixed precision, Sec. 2.2 last paragraph);
  *               QCD_PREC_F64: everything in FP64.
  *   rhs_tile    right-hand sides solved together (0 = library choice).
+ *   dfl         1 = use the deflated preconditioner once qcd_deflation_setup
+ *               has built the subspace (FP32 inner precision only):
+ *               M rho = Phi A^-1 Phi^+ rho + M_SAP(P_L rho), Sec. 2.2 local
+ *               deflation; the deflation blocks are the SAP blocks.
+ *   dfl_little_iters  steps of the block-Jacobi preconditioned GCR that
+ *               approximates A^-1 on the little vectors.
+ *   dfl_gen_iters  subspace generation: 0 = every inverse-iteration round
+ *               applies M_SAP; k > 0 = the first round applies M_SAP and the
+ *               later rounds k iterations of the deflated SAP-GCR solver.
  *   sap_half    FP32 SAP only: 1 = the block's links and clover term are held
  *               as 16-bit copies in shared memory during a block solve (the
  *               preconditioner changes by their rounding; the outer flexible
@@ -89,6 +98,9 @@ typedef struct {
   int precision;
   int rhs_tile;
   int sap_half;
+  int dfl;
+  int dfl_little_iters;
+  int dfl_gen_iters;
 } qcd_solver_params;
 
 /* Per right-hand-side outcome of a solve. */
@@ -118,7 +130,8 @@ qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int U_on_device, double
                           int time_bc);
 
 /* Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
- * restart_drop 1e-5, precision F32, rhs_tile 0, sap_half 0. */
+ * restart_drop 1e-5, precision F32, rhs_tile 0, sap_half 0, dfl 1,
+ * dfl_little_iters 16, dfl_gen_iters 0. */
 void qcd_default_params(qcd_solver_params* p);
 qcd_status qcd_set_params(qcd_ctx* ctx, const qcd_solver_params* p);
 
@@ -169,6 +182,27 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_ex
  * on spins 0,1 and block 1 on spins 2,3, index 3*(spin & 1) + colour. */
 qcd_status qcd_get_clover(qcd_ctx* ctx, double* out);
 
+/* Local deflation (Sec. 2.2).  Builds the deflation subspace on the SAP
+ * blocks from ns random global fields init (device, canonical FP64, ns
+ * spinors; the caller draws them): block Gram-Schmidt, then n_inv rounds of
+ * the inverse iteration phi -> M_SAP phi followed by block Gram-Schmidt; then
+ * the little Dirac operator A = (phi_k^b, D phi_l^b') (eq. little) on the
+ * block and its 8 neighbours, and the FP64 Gauss-Jordan inverses of its
+ * diagonal blocks.  1 <= ns <= 32; SAP block extents >= 2 in every
+ * direction.  Setting new parameters with a different block size discards
+ * the subspace.  Returns QCD_ERR_BREAKDOWN if a diagonal block is singular. */
+qcd_status qcd_deflation_setup(qcd_ctx* ctx, const double* init, int ns, int n_inv);
+/* The deflation fields as ns canonical FP64 spinors (device). */
+qcd_status qcd_deflation_fields(qcd_ctx* ctx, double* out);
+/* The little Dirac operator as host FP64 complex [block][9][ns][ns]: part 0
+ * couples a block to itself, 1 + 2 mu to its neighbour at +mu, 2 + 2 mu to
+ * the one at -mu; blocks are numbered ((bt*nbz + bz)*nby + by)*nbx + bx. */
+qcd_status qcd_deflation_little_matrix(qcd_ctx* ctx, double* out);
+/* Little vectors (host FP64 complex [n][block][ns]): mode 0: out = A in;
+ * mode 1: out = the m-step block-Jacobi preconditioned GCR approximation of
+ * A^-1 in used by the preconditioner. */
+qcd_status qcd_deflation_little(qcd_ctx* ctx, const double* in, double* out, int n, int mode, int m);
+
 /* Kernel timing (no counterpart in the paper; measurement support).  While
  * enabled, every kernel launch of the library on the context's stream is
  * bracketed by CUDA events.  qcd_profile_read synchronises the stream and
@@ -176,7 +210,7 @@ qcd_status qcd_get_clover(qcd_ctx* ctx, double* out);
  * the algorithmic bytes they had to move (each input word read once, each
  * output word written once), then clears the records.
  * Families: "dslash_f64", "dslash_f32", "sap_f64", "sap_f32", "blas",
- * "layout", "contract". */
+ * "layout", "contract", "deflation". */
 typedef struct {
   char name[24];
   int launches;

@@ -77,7 +77,8 @@ ProfScope::~ProfScope() {
   if (idx >= 0) cudaEventRecord(c->prof[idx].b, c->stream);
 }
 
-static const char* kFamName[FAM_N] = {"dslash_f64", "dslash_f32", "sap_f64", "sap_f32", "blas", "layout", "contract"};
+static const char* kFamName[FAM_N] = {"dslash_f64", "dslash_f32", "sap_f64", "sap_f32", "blas",
+                                      "layout",     "contract",   "deflation"};
 
 namespace {
 
@@ -116,6 +117,9 @@ qcd_status validate_params(const qcd_ctx* c, const qcd_solver_params* p) {
   ARG_CHECK(p->precision == QCD_PREC_F64 || p->precision == QCD_PREC_F32, "unknown precision %d", p->precision);
   ARG_CHECK(p->rhs_tile >= 0, "rhs_tile must be >= 0");
   ARG_CHECK(p->sap_half == 0 || p->sap_half == 1, "sap_half must be 0 or 1");
+  ARG_CHECK(p->dfl == 0 || p->dfl == 1, "dfl must be 0 or 1");
+  ARG_CHECK(p->dfl_little_iters >= 1 && p->dfl_little_iters <= 64, "dfl_little_iters must be in [1, 64]");
+  ARG_CHECK(p->dfl_gen_iters >= 0 && p->dfl_gen_iters <= 64, "dfl_gen_iters must be in [0, 64]");
   return QCD_OK;
 }
 
@@ -155,6 +159,9 @@ void qcd_default_params(qcd_solver_params* p) {
   p->precision = QCD_PREC_F32;
   p->rhs_tile = 0;
   p->sap_half = 0;
+  p->dfl = 1;
+  p->dfl_little_iters = 16;
+  p->dfl_gen_iters = 0;
 }
 
 qcd_status qcd_create(qcd_ctx** out, const int dims[4], void* cuda_stream) {
@@ -204,6 +211,7 @@ void qcd_destroy(qcd_ctx* c) {
   devbuf_free(c->contract);
   devbuf_free(c->stage);
   if (c->host_scal) cudaFreeHost(c->host_scal);
+  dfl_free(c);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -236,6 +244,9 @@ qcd_status qcd_load_gauge(qcd_ctx* c, const double* U, int U_on_device, double c
 qcd_status qcd_set_params(qcd_ctx* c, const qcd_solver_params* p) {
   ARG_CHECK(c != nullptr && p != nullptr, "null argument");
   QCD_TRY(validate_params(c, p));
+  bool same_blocks = true;
+  for (int mu = 0; mu < 4; mu++) same_blocks = same_blocks && p->block[mu] == c->params.block[mu];
+  if (!same_blocks) dfl_free(c);
   c->params = *p;
   return QCD_OK;
 }
@@ -450,6 +461,60 @@ qcd_status qcd_profile_read(qcd_ctx* c, qcd_kernel_time* out, int max, int* n) {
   }
   *n = k;
   return QCD_OK;
+}
+
+qcd_status qcd_deflation_setup(qcd_ctx* c, const double* init, int ns, int n_inv) {
+  QCD_TRY(check_ready(c));
+  ARG_CHECK(init != nullptr, "null argument");
+  ARG_CHECK(ns >= 1 && ns <= 32, "ns must be in [1, 32]");
+  ARG_CHECK(n_inv >= 0 && n_inv <= 32, "n_inv must be in [0, 32]");
+  for (int mu = 0; mu < 4; mu++)
+    ARG_CHECK(c->params.block[mu] >= 2, "deflation needs block extents >= 2 (direction %d)", mu);
+  QCD_TRY(dfl_setup(c, init, ns, n_inv));
+  QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
+  return QCD_OK;
+}
+
+qcd_status qcd_deflation_fields(qcd_ctx* c, double* out) {
+  QCD_TRY(check_ready(c));
+  ARG_CHECK(out != nullptr, "null argument");
+  if (!dfl_ready(c)) {
+    qcd_set_error("no deflation subspace");
+    return QCD_ERR_STATE;
+  }
+  QCD_TRY(layout_spinor_export(c, dfl_phi(c), out, QCD_PREC_F32, dfl_ns(c)));
+  QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
+  return QCD_OK;
+}
+
+qcd_status qcd_deflation_little_matrix(qcd_ctx* c, double* out) {
+  QCD_TRY(check_ready(c));
+  ARG_CHECK(out != nullptr, "null argument");
+  if (!dfl_ready(c)) {
+    qcd_set_error("no deflation subspace");
+    return QCD_ERR_STATE;
+  }
+  const size_t n = (size_t)dfl_nblk(c) * 9 * dfl_ns(c) * dfl_ns(c);
+  std::vector<float2> h(n);
+  QCD_CUDA_OK(cudaMemcpyAsync(h.data(), dfl_little(c), sizeof(float2) * n, cudaMemcpyDeviceToHost, c->stream));
+  QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < n; i++) {
+    out[2 * i] = h[i].x;
+    out[2 * i + 1] = h[i].y;
+  }
+  return QCD_OK;
+}
+
+qcd_status qcd_deflation_little(qcd_ctx* c, const double* in, double* out, int n, int mode, int m) {
+  QCD_TRY(check_ready(c));
+  ARG_CHECK(in && out && n >= 1, "bad argument");
+  ARG_CHECK(mode == 0 || mode == 1, "mode must be 0 or 1");
+  ARG_CHECK(m >= 1 && m <= 64, "m must be in [1, 64]");
+  if (!dfl_ready(c)) {
+    qcd_set_error("no deflation subspace");
+    return QCD_ERR_STATE;
+  }
+  return dfl_little_host(c, in, out, n, mode, m);
 }
 
 qcd_status qcd_get_clover(qcd_ctx* c, double* out) {

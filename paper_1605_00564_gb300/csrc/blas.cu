@@ -308,6 +308,47 @@ __global__ void __launch_bounds__(GS_TPB) k_multi_dot(const char* __restrict__ c
   }
 }
 
+// Same result with per-thread register accumulators: each thread walks its
+// sites (grid-stride) keeping one accumulator per j, so the CTA reduction
+// happens once per j per CTA instead of once per j per 256 sites.
+template <typename X, int KMAX>
+__global__ void __launch_bounds__(GS_TPB) k_multi_dot_acc(const char* __restrict__ chi, size_t jstride, int k, int V,
+                                                           double2* __restrict__ part, const int* mask) {
+  __shared__ double sh[2 * 32];
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  using R = typename X::R;
+  const size_t roff = (size_t)rhs * X::bytes * V;
+  R ar[KMAX], ai[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; j++) ar[j] = ai[j] = (R)0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+    Cplx<R> ck[12];
+#pragma unroll
+    for (int q = 0; q < 6; q++) X::ld(chi + k * jstride + roff, V, q, s, ck[2 * q], ck[2 * q + 1]);
+#pragma unroll
+    for (int j = 0; j < KMAX; j++) {
+      if (j < k) {
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+          Cplx<R> a, b;
+          X::ld(chi + j * jstride + roff, V, q, s, a, b);
+          ar[j] += a.re * ck[2 * q].re + a.im * ck[2 * q].im + b.re * ck[2 * q + 1].re + b.im * ck[2 * q + 1].im;
+          ai[j] += a.re * ck[2 * q].im - a.im * ck[2 * q].re + b.re * ck[2 * q + 1].im - b.im * ck[2 * q + 1].re;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KMAX; j++) {
+    if (j < k) {
+      double v[2] = {(double)ar[j], (double)ai[j]};
+      block_sum_n<2>(v, sh);
+      if (threadIdx.x == 0) part[((size_t)rhs * k + j) * gridDim.x + blockIdx.x] = make_double2(v[0], v[1]);
+    }
+  }
+}
+
 // out[j*nrhs + r] = sum over g of part[r][j][g] (fixed order)
 __global__ void __launch_bounds__(RED_TPB) k_sum_parts(const double2* __restrict__ part, int nj, int G,
                                                        double2* __restrict__ out, int nrhs, const int* mask) {
@@ -483,16 +524,22 @@ qcd_status blas_convert(qcd_ctx* c, const void* in, int pin, void* out, int pout
 qcd_status blas_gs_dots(qcd_ctx* c, const void* chi, int prec, size_t jstride, int k, int nrhs, double* dots_dev,
                         const int* mask, int nactive) {
   if (k <= 0) return QCD_OK;
-  const int G = (c->g.V + GS_TPB - 1) / GS_TPB;
+  const int G = red_grid(c);
   QCD_TRY(devbuf_ensure(c->red, (size_t)G * k * nrhs * sizeof(double2)));
   const double vb = prec == QCD_PREC_F64 ? 192 : 96;
   ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * (k + 1) * vb, (double)c->g.V * nactive * k * 48, 2);
-  if (prec == QCD_PREC_F64)
-    k_multi_dot<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((const char*)chi, jstride, k, c->g.V,
-                                                            (double2*)c->red.p, mask);
-  else
-    k_multi_dot<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((const char*)chi, jstride, k, c->g.V,
-                                                            (double2*)c->red.p, mask);
+  const dim3 grid(G, nrhs);
+  const char* cp = (const char*)chi;
+  double2* pp = (double2*)c->red.p;
+  if (prec == QCD_PREC_F64) {
+    if (k <= 8) k_multi_dot_acc<PD, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+    else if (k <= 16) k_multi_dot_acc<PD, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+    else k_multi_dot_acc<PD, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+  } else {
+    if (k <= 8) k_multi_dot_acc<PF, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+    else if (k <= 16) k_multi_dot_acc<PF, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+    else k_multi_dot_acc<PF, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+  }
   k_sum_parts<<<dim3(k, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, k, G, (double2*)dots_dev, nrhs,
                                                         mask);
   QCD_CUDA_OK(cudaGetLastError());

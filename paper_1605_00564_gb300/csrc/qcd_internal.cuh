@@ -312,7 +312,7 @@ qcd_status devbuf_ensure(DevBuf& b, size_t bytes);
 void devbuf_free(DevBuf& b);
 
 // kernel families of the timing records (qcd_profile_read)
-enum ProfFam { FAM_DSLASH_D, FAM_DSLASH_F, FAM_SAP_D, FAM_SAP_F, FAM_BLAS, FAM_LAYOUT, FAM_CONTRACT, FAM_N };
+enum ProfFam { FAM_DSLASH_D, FAM_DSLASH_F, FAM_SAP_D, FAM_SAP_F, FAM_BLAS, FAM_LAYOUT, FAM_CONTRACT, FAM_DFL, FAM_N };
 
 struct ProfRec {
   int fam, kernels;
@@ -343,6 +343,7 @@ struct qcd_ctx {
   DevBuf stage;       // staging for host <-> device copies
   double* host_scal = nullptr;   // pinned mirror of scalars
   size_t host_scal_bytes = 0;
+  void* dfl = nullptr;           // deflation state (dfl.cu)
 };
 
 // Brackets the launches issued in its scope with CUDA events when profiling
@@ -389,7 +390,19 @@ qcd_status blas_gs_finish(qcd_ctx* c, void* chik, int prec, const double* inv_de
 qcd_status blas_xmy(qcd_ctx* c, const void* x, const void* y, void* out, int prec, int nrhs, const int* mask);
 
 // SAP preconditioner: psi = M_SAP rho (rho is overwritten), precision prec
+// accumulate != 0: psi += M_SAP rho instead of psi = M_SAP rho
 qcd_status sap_apply(qcd_ctx* c, void* rho, void* psi, void* delta, int prec, int nrhs, const int* mask,
-                     int nactive);
+                     int nactive, int accumulate = 0);
+
+// deflation (dfl.cu)
+qcd_status dfl_setup(qcd_ctx* c, const double* init_dev, int ns, int n_inv);
+qcd_status dfl_low_mode(qcd_ctx* c, const void* rho, void* x, int n, const int* mask, int nactive, int m);
+qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int mode, int m);
+void dfl_free(qcd_ctx* c);
+int dfl_ready(qcd_ctx* c);
+int dfl_ns(qcd_ctx* c);
+int dfl_nblk(qcd_ctx* c);
+void* dfl_phi(qcd_ctx* c);
+void* dfl_little(qcd_ctx* c);
 
 size_t spinor_bytes(const qcd_ctx* c, int prec);

@@ -215,9 +215,12 @@ template <typename S>
 struct Stage;
 template <>
 struct Stage<float> {
-  using W = float4;
+  using W = float4;   // four reals
+  using C = float2;   // one complex
   static __device__ inline W put(float4 v) { return v; }
   static __device__ inline float4 get(W w) { return w; }
+  static __device__ inline C putc(Cplx<float> z) { return make_float2(z.re, z.im); }
+  static __device__ inline Cplx<float> getc(C w) { return cmk(w.x, w.y); }
 };
 template <>
 struct Stage<__half> {
@@ -234,18 +237,21 @@ struct Stage<__half> {
     float2 b = __half22float2(*reinterpret_cast<__half2*>(&w.y));
     return make_float4(a.x, a.y, b.x, b.y);
   }
+  using C = __half2;
+  static __device__ inline C putc(Cplx<float> z) { return __floats2half2_rn(z.re, z.im); }
+  static __device__ inline Cplx<float> getc(C w) {
+    float2 a = __half22float2(w);
+    return cmk(a.x, a.y);
+  }
 };
 
+// the full 3x3 link (staged with its third row already reconstructed)
 template <typename S>
-__device__ inline SU3<float> smem_link(const typename Stage<S>::W* lk, int vb, int mu, int l) {
-  const typename Stage<S>::W* p = lk + (size_t)mu * 3 * vb;
-  float4 a = Stage<S>::get(p[l]), b = Stage<S>::get(p[vb + l]), c = Stage<S>::get(p[2 * vb + l]);
+__device__ inline SU3<float> smem_link(const typename Stage<S>::C* lk, int vb, int mu, int l) {
+  const typename Stage<S>::C* p = lk + (size_t)mu * 9 * vb;
   SU3<float> U;
-  U.m[0][0] = cmk(a.x, a.y); U.m[0][1] = cmk(a.z, a.w); U.m[0][2] = cmk(b.x, b.y);
-  U.m[1][0] = cmk(b.z, b.w); U.m[1][1] = cmk(c.x, c.y); U.m[1][2] = cmk(c.z, c.w);
-  U.m[2][0] = conj(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
-  U.m[2][1] = conj(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
-  U.m[2][2] = conj(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
+#pragma unroll
+  for (int k = 0; k < 9; k++) U.m[k / 3][k % 3] = Stage<S>::getc(p[(size_t)k * vb + l]);
   return U;
 }
 
@@ -267,7 +273,7 @@ __device__ inline Spinor<float> smem_clover_apply(const typename Stage<S>::W* cl
 }
 
 template <typename S, int MU>
-__device__ inline void smem_block_hop(Spinor<float>& p, const Cplx<float>* r_s, const typename Stage<S>::W* lk,
+__device__ inline void smem_block_hop(Spinor<float>& p, const Cplx<float>* r_s, const typename Stage<S>::C* lk,
                                       const SapGeom& sg, int l, const int lc[4], float scale) {
   if (lc[MU] < sg.b[MU] - 1) {
     HalfSpinor<float> h = project<MU, -1>(smem_load(r_s, sg.vb, l + sg.lst[MU]));
@@ -287,11 +293,12 @@ __global__ void __launch_bounds__(MAXT, MINB)
                      const float4* __restrict__ gauge, const float4* __restrict__ clover, Geom g, SapGeom sg,
                      int colour, int gather, int psi_init, float kappa, int nmr, int nrhs, const int* mask) {
   using W = typename Stage<S>::W;
+  using CW = typename Stage<S>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int vb = sg.vb;
   Cplx<float>* r_s = (Cplx<float>*)smem_raw;
-  W* lk_s = (W*)(smem_raw + (size_t)12 * vb * sizeof(Cplx<float>));
-  W* cl_s = lk_s + (size_t)12 * vb;
+  CW* lk_s = (CW*)(smem_raw + (size_t)12 * vb * sizeof(Cplx<float>));     // [4][9][vb]
+  W* cl_s = (W*)(lk_s + (size_t)36 * vb);                                 // [18][vb]
   __shared__ float red[3][32];
 
   const int rhs = blockIdx.y;
@@ -325,11 +332,13 @@ __global__ void __launch_bounds__(MAXT, MINB)
   c[3] = bz * sg.b[3] + lc[3];
   const int s = ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
 
-  // stage this site's four links (rows 0, 1) and its clover term
+  // stage this site's four links (full 3x3) and its clover term
 #pragma unroll
-  for (int mu = 0; mu < 4; mu++)
+  for (int mu = 0; mu < 4; mu++) {
+    SU3<float> U = FieldsF::load_link(gauge, g.V, mu, s);
 #pragma unroll
-    for (int k = 0; k < 3; k++) lk_s[(size_t)(3 * mu + k) * vb + l] = Stage<S>::put(__ldg(gauge + (size_t)(3 * mu + k) * g.V + s));
+    for (int k = 0; k < 9; k++) lk_s[(size_t)(9 * mu + k) * vb + l] = Stage<S>::putc(U.m[k / 3][k % 3]);
+  }
 #pragma unroll
   for (int k = 0; k < 18; k++) cl_s[(size_t)k * vb + l] = Stage<S>::put(__ldg(clover + (size_t)k * g.V + s));
 
@@ -400,7 +409,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
 
 template <typename F>
 qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const void* gauge, const void* clover,
-                         int nrhs, const int* mask, int nactive) {
+                         int nrhs, const int* mask, int nactive, int accumulate) {
   const qcd_solver_params& P = c->params;
   SapGeom sg;
   sg.vb = 1;
@@ -438,20 +447,21 @@ qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const vo
   // FP32 with blocks of at most 256 sites: the shared-memory-resident kernel
   const bool resident = sizeof(typename F::R) == 4 && sg.vb <= 256;
   auto kres = P.sap_half ? k_sap_sweep_smem<__half, 256, 2> : k_sap_sweep_smem<float, 256, 1>;
-  const size_t smem_res = (size_t)sg.vb * (96 + (P.sap_half ? 96 + 144 : 192 + 288));
+  const size_t smem_res = (size_t)sg.vb * (96 + (P.sap_half ? 144 + 144 : 288 + 288));
   if (resident)
     QCD_CUDA_OK(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res));
   for (int cy = 0; cy < P.ncy; cy++)
     for (int col = 0; col < 2; col++) {
-      const double bytes_site = sb * (2 + (cy == 0 ? 1 : 2) + 1 + face) + 4 * lb + cb;
+      const int first = cy == 0 && !accumulate;
+      const double bytes_site = sb * (2 + (first ? 1 : 2) + 1 + face) + 4 * lb + cb;
       ProfScope ps(c, fam, half * nactive * bytes_site, half * nactive * flops_site);
       if (resident)
         kres<<<grid, sg.vb, smem_res, c->stream>>>(rho, psi, delta, (const float4*)gauge, (const float4*)clover, c->g,
-                                                   sg, col, !(cy == 0 && col == 0), cy == 0, (float)c->kappa, P.nmr,
+                                                   sg, col, !(cy == 0 && col == 0), first, (float)c->kappa, P.nmr,
                                                    nrhs, mask);
       else
         kern<<<grid, sg.vb, smem, c->stream>>>(rho, psi, delta, gauge, clover, c->g, sg, col, !(cy == 0 && col == 0),
-                                               cy == 0, (typename F::R)c->kappa, P.nmr, nrhs, mask);
+                                               first, (typename F::R)c->kappa, P.nmr, nrhs, mask);
       QCD_CUDA_OK(cudaGetLastError());
     }
   return QCD_OK;
@@ -460,10 +470,10 @@ qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const vo
 }  // namespace
 
 qcd_status sap_apply(qcd_ctx* c, void* rho, void* psi, void* delta, int prec, int nrhs, const int* mask,
-                     int nactive) {
+                     int nactive, int accumulate) {
   if (prec == QCD_PREC_F64)
     return launch_sweeps<FieldsD>(c, (char*)rho, (char*)psi, (char*)delta, c->gaugeD.p, c->cloverD.p, nrhs, mask,
-                                  nactive);
+                                  nactive, accumulate);
   return launch_sweeps<FieldsF>(c, (char*)rho, (char*)psi, (char*)delta, c->gaugeF.p, c->cloverF.p, nrhs, mask,
-                                nactive);
+                                nactive, accumulate);
 }

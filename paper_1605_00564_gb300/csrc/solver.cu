@@ -110,6 +110,7 @@ qcd_status fetch(qcd_ctx* c, void* host, const void* dev, size_t bytes) {
 qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
   const qcd_solver_params& P = c->params;
   const int nkv = P.nkv, prec = P.precision;
+  const bool use_dfl = P.dfl && dfl_ready(c) && prec == QCD_PREC_F32;
   Work w;
   QCD_TRY(get_work(c, n, nkv, prec, w));
   const size_t VI = spinor_bytes(c, prec) * n;
@@ -201,7 +202,15 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
       char* phik = w.phi + VI * k;
       char* chik = w.chi + VI * k;
       if (k == 0) QCD_TRY(blas_convert(c, w.rho, QCD_PREC_F64, w.rhoS, prec, n, w.mask));
-      QCD_TRY(sap_apply(c, w.rhoS, phik, w.delta, prec, n, w.mask, nin_now));
+      if (use_dfl) {
+        // deflated preconditioner: phi_k = Phi A^-1 Phi^+ rho + M_SAP(rho - D Phi A^-1 Phi^+ rho)
+        QCD_TRY(dfl_low_mode(c, w.rhoS, phik, n, w.mask, nin_now, P.dfl_little_iters));
+        QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now));
+        QCD_TRY(blas_xmy(c, w.rhoS, chik, w.rhoS, prec, n, w.mask));
+        QCD_TRY(sap_apply(c, w.rhoS, phik, w.delta, prec, n, w.mask, nin_now, 1));
+      } else {
+        QCD_TRY(sap_apply(c, w.rhoS, phik, w.delta, prec, n, w.mask, nin_now));
+      }
       QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now));
       // Gram-Schmidt against chi_0..chi_{k-1}, normalisation, residual update;
       // the update also writes the next preconditioner input rhoS

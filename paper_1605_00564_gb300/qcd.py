@@ -28,6 +28,7 @@ EXPORTS = (
     "qcd_status_string", "qcd_last_error", "qcd_create", "qcd_destroy", "qcd_load_gauge",
     "qcd_default_params", "qcd_set_params", "qcd_apply_dirac", "qcd_apply_sap", "qcd_solve",
     "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_get_clover", "qcd_profile_enable", "qcd_profile_read",
+    "qcd_deflation_setup", "qcd_deflation_fields", "qcd_deflation_little_matrix", "qcd_deflation_little",
 )
 
 
@@ -41,7 +42,8 @@ class SolverParams(ctypes.Structure):
     _fields_ = [
         ("block", ctypes.c_int * 4), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int), ("nkv", ctypes.c_int),
         ("max_outer", ctypes.c_int), ("restart_drop", ctypes.c_double), ("precision", ctypes.c_int),
-        ("rhs_tile", ctypes.c_int), ("sap_half", ctypes.c_int),
+        ("rhs_tile", ctypes.c_int), ("sap_half", ctypes.c_int), ("dfl", ctypes.c_int),
+        ("dfl_little_iters", ctypes.c_int), ("dfl_gen_iters", ctypes.c_int),
     ]
 
 
@@ -90,6 +92,10 @@ def load_library(path=LIB_PATH):
     L.qcd_nucleon_2pt.argtypes = [vp, vp, ip, dp, i]
     L.qcd_ama_nucleon_2pt.argtypes = [vp, ip, i, i, d, d, dp, dp, ctypes.POINTER(RhsStats)]
     L.qcd_get_clover.argtypes = [vp, vp]
+    L.qcd_deflation_setup.argtypes = [vp, vp, i, i]
+    L.qcd_deflation_fields.argtypes = [vp, vp]
+    L.qcd_deflation_little_matrix.argtypes = [vp, dp]
+    L.qcd_deflation_little.argtypes = [vp, dp, dp, i, i, i]
     L.qcd_profile_enable.argtypes = [vp, i]
     L.qcd_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), i, ip]
     for name in EXPORTS:
@@ -236,6 +242,40 @@ class Lattice:
         _check(_lib.qcd_profile_read(self._ctx, buf, 16, ctypes.byref(n)))
         return {buf[k].name.decode(): {"launches": buf[k].launches, "ms": buf[k].ms, "bytes": buf[k].bytes,
                                        "flops": buf[k].flops} for k in range(n.value)}
+
+    # ----------------------------------------------------------------------
+    def deflation_setup(self, init, n_inv):
+        """Build the deflation subspace from init (CUDA complex128, (ns,)+spinor shape)."""
+        init = init.contiguous()
+        _check(_lib.qcd_deflation_setup(self._ctx, _dev_ptr(init), int(init.shape[0]), int(n_inv)))
+        self.dfl_ns = int(init.shape[0])
+
+    def deflation_fields(self):
+        import torch
+        out = torch.empty(self.spinor_shape(self.dfl_ns), dtype=torch.complex128, device="cuda")
+        _check(_lib.qcd_deflation_fields(self._ctx, _dev_ptr(out)))
+        return out
+
+    def n_blocks(self):
+        b = list(self.params.block)
+        return (self.T // b[0]) * (self.X // b[1]) * (self.Y // b[2]) * (self.Z // b[3])
+
+    def deflation_little_matrix(self):
+        """A as numpy complex [block][9][ns][ns]."""
+        nb, ns = self.n_blocks(), self.dfl_ns
+        out = np.zeros((nb, 9, ns, ns, 2))
+        _check(_lib.qcd_deflation_little_matrix(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def deflation_little(self, v, mode, m=16):
+        """mode 0: A v; mode 1: m-step approximation of A^-1 v.  v: numpy complex [n, block, ns]."""
+        v = np.ascontiguousarray(v, dtype=np.complex128)
+        n = v.shape[0]
+        out = np.zeros(v.shape + (2,))
+        vin = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1))
+        _check(_lib.qcd_deflation_little(self._ctx, vin.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, int(mode), int(m)))
+        return out[..., 0] + 1j * out[..., 1]
 
     def get_clover(self):
         """A(x) as a CUDA complex128 tensor [V, 2, 6, 6]."""
