@@ -204,7 +204,7 @@ def barrier(ws):
 def kernel_traffic(family_kernel):
     """DRAM bytes per unit of the dominant kernel from the committed ncu summary,
     if it was taken on the current source of that kernel; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         rec = json.load(open(path))[family_kernel]
     except Exception:
