@@ -182,6 +182,30 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_ex
  * on spins 0,1 and block 1 on spins 2,3, index 3*(spin & 1) + colour. */
 qcd_status qcd_get_clover(qcd_ctx* ctx, double* out);
 
+/* Allocation-free nucleon two-point function (no counterpart in the paper:
+ * an interface for callers that cannot allocate device memory where they
+ * need the correlator - inside a stream capture, under a host application's
+ * own device allocator or fixed arena, or in a loop that must not take an
+ * allocation's implicit synchronisation).  It computes what qcd_nucleon_2pt
+ * computes, needs no context, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   dims {T, X, Y, Z}; time_bc +1 / -1; prop: device, canonical FP64, the 12
+ *   spinors of a point source (rhs = 3*spin + colour); src {t, x, y, z};
+ *   corr: DEVICE memory of 2*T*2 doubles, [p][t][re/im] as in qcd_nucleon_2pt;
+ *   precision QCD_PREC_F64 or QCD_PREC_F32; cuda_stream: the stream to use.
+ * The work is only enqueued on cuda_stream; corr is ready when it completes.
+ * Scratch: a fixed 4 MiB device array inside the library (resident on every
+ * GPU that loads it until the process exits) holds the per-CTA partial sums,
+ * which limits the lattice to V / ns <= 131072, ns being the largest power of
+ * two <= 32 dividing X*Y*Z (e.g. up to 4,194,304 sites when 32 divides X*Y*Z);
+ * larger lattices return QCD_ERR_ARG before any launch.  The first call on a
+ * device looks up the array's device address (and sets kernel attributes); make
+ * that first call before capturing a stream.  All calls share the array:
+ * calls that overlap on the GPU (different streams, not ordered) race on it
+ * and give wrong results. */
+qcd_status qcd_nucleon_2pt_noalloc(const int dims[4], int time_bc, const double* prop, const int src[4],
+                                   double* corr, int precision, void* cuda_stream);
+
 /* Local deflation (Sec. 2.2).  Builds the deflation subspace on the SAP
  * blocks from ns random global fields init (device, canonical FP64, ns
  * spinors; the caller draws them): block Gram-Schmidt, then n_inv rounds of

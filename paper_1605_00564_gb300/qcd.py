@@ -29,6 +29,7 @@ EXPORTS = (
     "qcd_default_params", "qcd_set_params", "qcd_apply_dirac", "qcd_apply_sap", "qcd_solve",
     "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_get_clover", "qcd_profile_enable", "qcd_profile_read",
     "qcd_deflation_setup", "qcd_deflation_fields", "qcd_deflation_little_matrix", "qcd_deflation_little",
+    "qcd_nucleon_2pt_noalloc",
 )
 
 
@@ -92,6 +93,7 @@ def load_library(path=LIB_PATH):
     L.qcd_nucleon_2pt.argtypes = [vp, vp, ip, dp, i]
     L.qcd_ama_nucleon_2pt.argtypes = [vp, ip, i, i, d, d, dp, dp, ctypes.POINTER(RhsStats)]
     L.qcd_get_clover.argtypes = [vp, vp]
+    L.qcd_nucleon_2pt_noalloc.argtypes = [ip, i, vp, ip, vp, i, vp]
     L.qcd_deflation_setup.argtypes = [vp, vp, i, i]
     L.qcd_deflation_fields.argtypes = [vp, vp]
     L.qcd_deflation_little_matrix.argtypes = [vp, dp]
@@ -116,6 +118,19 @@ def _dev_ptr(t):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def nucleon_2pt_noalloc(dims, prop, src, corr, precision="f64", time_bc=-1, stream=None):
+    """Enqueue the allocation-free contraction: prop (CUDA complex128, 12 spinors,
+    canonical) -> corr (CUDA float64 tensor of 2*T*2 values, written in place).
+    The library allocates nothing; the caller owns both buffers."""
+    import torch
+    L = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(L.qcd_nucleon_2pt_noalloc((ctypes.c_int * 4)(*dims), int(time_bc), _dev_ptr(prop),
+                                     (ctypes.c_int * 4)(*src), _dev_ptr(corr), PREC[precision],
+                                     ctypes.c_void_p(s.cuda_stream)))
+    return corr
 
 
 class Lattice:
