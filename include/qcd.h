@@ -86,7 +86,9 @@ typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
  *   sap_half    FP32 SAP only: 1 = the block's links and clover term are held
  *               as 16-bit copies in shared memory during a block solve (the
  *               preconditioner changes by their rounding; the outer flexible
- *               GCR is unaffected in what it converges to); 0 = FP32 copies.
+ *               GCR is unaffected in what it converges to); 2 = in addition the
+ *               block residual read by neighbouring sites is held as bf16;
+ *               0 = FP32 copies.
  */
 typedef struct {
   int block[4];
@@ -153,6 +155,16 @@ qcd_status qcd_apply_sap(qcd_ctx* ctx, const double* eta, double* psi, int nrhs,
 qcd_status qcd_solve(qcd_ctx* ctx, const double* eta, double* psi, int nrhs, const double* rel_tol,
                      qcd_rhs_stats* stats);
 
+/* Several lattices (contexts of different sizes) solved in one call: each
+ * context's solve runs from its own host thread on its own stream, so the
+ * lattices' kernels overlap on the GPU.  Arrays of nctx entries; eta[i],
+ * psi[i] device canonical spinors of ctxs[i], rel_tol[i] host arrays of
+ * nrhs[i] tolerances, stats[i] host arrays or stats == NULL.  With nctx > 1
+ * every context needs a non-default stream.  Returns the first non-OK status
+ * in context order.  Errors of a context do not stop the others. */
+qcd_status qcd_solve_multi(qcd_ctx* const* ctxs, int nctx, const double* const* eta, double* const* psi,
+                           const int* nrhs, const double* const* rel_tol, qcd_rhs_stats* const* stats);
+
 /* Nucleon two-point function (eq. Nop, N = eps^{abc} (u^a^T C g5 d^b) u^c,
  * C = g0 g2, u = d) from one point-source propagator prop (device,
  * canonical, 12 spinors rhs = 3*spin + colour) with source src = {t,x,y,z}:
@@ -181,6 +193,37 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_ex
  * as [site][chirality 2][6][6] complex FP64 (device), chirality block 0 acting
  * on spins 0,1 and block 1 on spins 2,3, index 3*(spin & 1) + colour. */
 qcd_status qcd_get_clover(qcd_ctx* ctx, double* out);
+
+/* Differentiable nucleon correlator (Feynman-Hellmann).  Wilson normalisation:
+ * D_w = D / (2 kappa), kappa = 1 / (2 m0 + 8), S = D_w^-1; the isovector axial
+ * coupling adds +lambda g3 g5 to D_w for u and -lambda g3 g5 for d (the
+ * zero-momentum A_3 insertion of R_A, Sec. 2.3), taken at lambda = 0.
+ * qcd_fh_forward: solves the 12 point sources at src to tol, writes S (device,
+ * canonical FP64, 12 spinors) and C = tr[P+- <N N-bar>] (host [2][T][2], FP64,
+ * from S) as qcd_nucleon_2pt; stats: 12 entries or NULL.
+ * qcd_fh_gradient: for the upstream gradient gcorr (host [2][T][2]: dL/dRe C,
+ * dL/dIm C) of a real loss L, returns grad = {dL/dm0, dL/dlambda} (host) by the
+ * adjoint method: H = dL/dS from the contraction, Y = (D_w^+)^-1 H
+ * = 2 kappa g5 D^-1 g5 H (24 solves: u and d), dL/dtheta = -Re sum tr[Y^+ dD_w S].
+ * prop is the S returned by qcd_fh_forward; stats: 24 entries or NULL. */
+qcd_status qcd_fh_forward(qcd_ctx* ctx, const int src[4], double tol, double* prop, double* corr,
+                          qcd_rhs_stats* stats);
+qcd_status qcd_fh_gradient(qcd_ctx* ctx, const double* prop, const int src[4], const double* gcorr, double tol,
+                           double* grad, qcd_rhs_stats* stats);
+
+/* Autotuner (no counterpart in the paper; implementation parameters only).
+ * Times a solve of the nrhs device canonical sources eta to tol for each
+ * candidate SAP block shape (4^4, 8x4^3, 4^3x8, 4x8x4^2 where they tile the
+ * lattice), 16- or 32-bit SAP block copies, nkv in {16, 32} and rhs_tile in
+ * {nrhs, nrhs/2}, keeping ncy, nmr, precision and deflation as set; the
+ * fastest converged candidate becomes the context's parameters and is
+ * written to *best (may be NULL).  cache_path (may be NULL): a text file of
+ * earlier results, keyed by lattice, couplings, tolerance, nrhs and GPU name;
+ * a hit skips the timing.  Changing the block shape discards a deflation
+ * subspace.  Allocates one nrhs-spinor work buffer for the duration of the
+ * call. */
+qcd_status qcd_autotune(qcd_ctx* ctx, const double* eta, int nrhs, double tol, const char* cache_path,
+                        qcd_solver_params* best);
 
 /* Allocation-free nucleon two-point function (no counterpart in the paper:
  * an interface for callers that cannot allocate device memory where they

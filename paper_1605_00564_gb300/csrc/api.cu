@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <thread>
 #include <vector>
 
 #include "qcd_internal.cuh"
@@ -116,7 +117,7 @@ qcd_status validate_params(const qcd_ctx* c, const qcd_solver_params* p) {
   ARG_CHECK(p->restart_drop >= 0 && p->restart_drop < 1, "restart_drop must be in [0, 1)");
   ARG_CHECK(p->precision == QCD_PREC_F64 || p->precision == QCD_PREC_F32, "unknown precision %d", p->precision);
   ARG_CHECK(p->rhs_tile >= 0, "rhs_tile must be >= 0");
-  ARG_CHECK(p->sap_half == 0 || p->sap_half == 1, "sap_half must be 0 or 1");
+  ARG_CHECK(p->sap_half >= 0 && p->sap_half <= 2, "sap_half must be 0, 1 or 2");
   ARG_CHECK(p->dfl == 0 || p->dfl == 1, "dfl must be 0 or 1");
   ARG_CHECK(p->dfl_little_iters >= 1 && p->dfl_little_iters <= 64, "dfl_little_iters must be in [1, 64]");
   ARG_CHECK(p->dfl_gen_iters >= 0 && p->dfl_gen_iters <= 64, "dfl_gen_iters must be in [0, 64]");
@@ -314,6 +315,31 @@ qcd_status qcd_solve(qcd_ctx* c, const double* eta, double* psi, int nrhs, const
   }
   if (worst != QCD_OK) qcd_set_error("%d of %d right-hand sides did not converge", nbad, nrhs);
   return worst;
+}
+
+qcd_status qcd_solve_multi(qcd_ctx* const* ctxs, int nctx, const double* const* eta, double* const* psi,
+                           const int* nrhs, const double* const* rel_tol, qcd_rhs_stats* const* stats) {
+  ARG_CHECK(ctxs && nctx >= 1 && eta && psi && nrhs && rel_tol, "null argument");
+  for (int i = 0; i < nctx; i++) {
+    QCD_TRY(check_ready(ctxs[i]));
+    for (int j = 0; j < i; j++)
+      ARG_CHECK(ctxs[j] != ctxs[i], "context %d appears twice", i);
+    ARG_CHECK(nctx == 1 || ctxs[i]->stream != nullptr,
+              "qcd_solve_multi needs a non-default stream per context to run the lattices concurrently");
+  }
+  std::vector<qcd_status> rc(nctx, QCD_OK);
+  std::vector<std::thread> th;
+  int dev = 0;
+  QCD_CUDA_OK(cudaGetDevice(&dev));
+  for (int i = 0; i < nctx; i++)
+    th.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      rc[i] = qcd_solve(ctxs[i], eta[i], psi[i], nrhs[i], rel_tol[i], stats ? stats[i] : nullptr);
+    });
+  for (auto& t : th) t.join();
+  for (int i = 0; i < nctx; i++)
+    if (rc[i] != QCD_OK) return rc[i];
+  return QCD_OK;
 }
 
 qcd_status qcd_nucleon_2pt(qcd_ctx* c, const double* prop, const int src[4], double* corr, int precision) {

@@ -406,6 +406,98 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth(char* __restrict__ chi, size
   }
 }
 
+// Site-major form of k_gs_orth: a thread holds all 12 components of chi_k
+// for its site and walks the j < k vectors with independent loads (the j
+// loop is unrolled to KMAX), so many loads are in flight per thread.
+template <typename X, int KMAX>
+__global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, size_t jstride, int k,
+                                                        const double2* __restrict__ dots, const char* __restrict__ rho,
+                                                        int V, int nrhs, double2* __restrict__ part, const int* mask) {
+  __shared__ double sh[3 * 32];
+  __shared__ float2 w_s[KMAX];
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  using R = typename X::R;
+  if (threadIdx.x < KMAX && (int)threadIdx.x < k) {
+    double2 d = dots[(size_t)threadIdx.x * nrhs + rhs];
+    w_s[threadIdx.x] = make_float2((float)d.x, (float)d.y);
+  }
+  __syncthreads();
+  const size_t roff = (size_t)rhs * X::bytes * V;
+  char* ckp = chi + k * jstride + roff;
+  const char* rp = rho + (size_t)rhs * PD::bytes * V;
+  double n2 = 0, cr = 0, ci = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+    Cplx<R> a[12];
+#pragma unroll
+    for (int q = 0; q < 6; q++) X::ld(ckp, V, q, s, a[2 * q], a[2 * q + 1]);
+#pragma unroll
+    for (int j = 0; j < KMAX; j++) {
+      if (j < k) {
+        Cplx<R> u[12];
+#pragma unroll
+        for (int q = 0; q < 6; q++) X::ld(chi + j * jstride + roff, V, q, s, u[2 * q], u[2 * q + 1]);
+        const Cplx<R> w = cmk((R)w_s[j].x, (R)w_s[j].y);
+#pragma unroll
+        for (int q = 0; q < 12; q++) a[q] = a[q] - w * u[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; q++) X::st(ckp, V, q, s, a[2 * q], a[2 * q + 1]);
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      Cplx<double> x, y;
+      PD::ld(rp, V, q, s, x, y);
+      const Cplx<R> p0 = a[2 * q], p1 = a[2 * q + 1];
+      n2 += (double)(p0.re * p0.re + p0.im * p0.im + p1.re * p1.re + p1.im * p1.im);
+      cr += (double)p0.re * x.re + (double)p0.im * x.im + (double)p1.re * y.re + (double)p1.im * y.im;
+      ci += (double)p0.re * x.im - (double)p0.im * x.re + (double)p1.re * y.im - (double)p1.im * y.re;
+    }
+  }
+  double v[3] = {n2, cr, ci};
+  block_sum_n<3>(v, sh);
+  if (threadIdx.x == 0) {
+    double2* pp = part + (size_t)rhs * 2 * gridDim.x;
+    pp[blockIdx.x] = make_double2(v[0], 0.0);
+    pp[gridDim.x + blockIdx.x] = make_double2(v[1], v[2]);
+  }
+}
+
+// Site-major y (FP64) += sign sum_{j<nx} coef_j x_j (FP32)
+template <int KMAX>
+__global__ void __launch_bounds__(GS_TPB) k_caxpy_sm(char* __restrict__ y, const char* __restrict__ xbase, int nx,
+                                                      size_t xstride, const double2* __restrict__ coef, double sign,
+                                                      int V, int nrhs, const int* mask) {
+  __shared__ double2 c_s[KMAX];
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  if (threadIdx.x < KMAX && (int)threadIdx.x < nx) {
+    double2 c = coef[(size_t)threadIdx.x * nrhs + rhs];
+    c_s[threadIdx.x] = make_double2(sign * c.x, sign * c.y);
+  }
+  __syncthreads();
+  char* yb = y + (size_t)rhs * PD::bytes * V;
+  const size_t xoff = (size_t)rhs * PF::bytes * V;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+    Cplx<double> a[12];
+#pragma unroll
+    for (int q = 0; q < 6; q++) PD::ld(yb, V, q, s, a[2 * q], a[2 * q + 1]);
+#pragma unroll
+    for (int j = 0; j < KMAX; j++) {
+      if (j < nx) {
+        Cplx<float> u[12];
+#pragma unroll
+        for (int q = 0; q < 6; q++) PF::ld(xbase + j * xstride + xoff, V, q, s, u[2 * q], u[2 * q + 1]);
+        const Cplx<double> w = cmk(c_s[j].x, c_s[j].y);
+#pragma unroll
+        for (int q = 0; q < 12; q++) a[q] = a[q] + w * cmk((double)u[q].re, (double)u[q].im);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; q++) PD::st(yb, V, q, s, a[2 * q], a[2 * q + 1]);
+  }
+}
+
 // chi_k *= inv; rho -= ck * chi_k; rho_s = rho in the inner precision; partial |rho|^2
 template <typename X>
 __global__ void __launch_bounds__(GS_TPB) k_gs_finish(char* __restrict__ chik, const double* __restrict__ inv,
@@ -469,9 +561,19 @@ qcd_status blas_multi_caxpy(qcd_ctx* c, void* y, int py, const void* xbase, int 
   if (py == QCD_PREC_F64 && px == QCD_PREC_F64)
     k_multi_caxpy<PD, PD><<<g, 256, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride,
                                                     (const double2*)coef_dev, sign, c->g.V, nrhs, mask);
-  else if (py == QCD_PREC_F64 && px == QCD_PREC_F32)
-    k_multi_caxpy<PD, PF><<<g, 256, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride,
-                                                    (const double2*)coef_dev, sign, c->g.V, nrhs, mask);
+  else if (py == QCD_PREC_F64 && px == QCD_PREC_F32) {
+    const dim3 gs(red_grid(c), nrhs);
+    const double2* cf = (const double2*)coef_dev;
+    if (nx <= 8)
+      k_caxpy_sm<8><<<gs, GS_TPB, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride, cf, sign, c->g.V, nrhs,
+                                                  mask);
+    else if (nx <= 16)
+      k_caxpy_sm<16><<<gs, GS_TPB, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride, cf, sign, c->g.V,
+                                                   nrhs, mask);
+    else
+      k_caxpy_sm<32><<<gs, GS_TPB, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride, cf, sign, c->g.V,
+                                                   nrhs, mask);
+  }
   else if (py == QCD_PREC_F32 && px == QCD_PREC_F32)
     k_multi_caxpy<PF, PF><<<g, 256, 0, c->stream>>>((char*)y, (const char*)xbase, nx, xstride,
                                                     (const double2*)coef_dev, sign, c->g.V, nrhs, mask);
@@ -554,12 +656,19 @@ qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, 
   const double vb = prec == QCD_PREC_F64 ? 192 : 96;
   ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * ((k + 2) * vb + 192), (double)c->g.V * nactive * (k + 2) * 48,
                2);
+  const dim3 grid(G, nrhs);
+  char* cp = (char*)chi;
+  const double2* dp = (const double2*)dots_dev;
+  const char* rp = (const char*)rho;
+  double2* pp = (double2*)c->red.p;
   if (prec == QCD_PREC_F64)
-    k_gs_orth<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chi, jstride, k, (const double2*)dots_dev,
-                                                          (const char*)rho, c->g.V, nrhs, (double2*)c->red.p, mask);
+    k_gs_orth<PD><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+  else if (k <= 8)
+    k_gs_orth_sm<PF, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+  else if (k <= 16)
+    k_gs_orth_sm<PF, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
   else
-    k_gs_orth<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chi, jstride, k, (const double2*)dots_dev,
-                                                          (const char*)rho, c->g.V, nrhs, (double2*)c->red.p, mask);
+    k_gs_orth_sm<PF, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
   k_sum_parts<<<dim3(2, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 2, G, (double2*)n2c_dev, nrhs,
                                                         mask);
   QCD_CUDA_OK(cudaGetLastError());

@@ -20,6 +20,7 @@
 // One CTA per block and right-hand side, one thread per block site; the
 // block's residual lives in shared memory across the MR steps, the solution
 // increment x in registers.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "qcd_internal.cuh"
@@ -245,6 +246,40 @@ struct Stage<__half> {
   }
 };
 
+// Storage of the block residual shared between neighbouring threads:
+// FP32 complex, or bf16 pairs (FP32 exponent range, 8-bit mantissa; each
+// thread keeps its own residual in FP32 registers, only the neighbours'
+// contributions to p = D_L r see the rounding).
+template <bool BF>
+struct RStore;
+template <>
+struct RStore<false> {
+  using T = Cplx<float>;
+  static __device__ inline T put(Cplx<float> z) { return z; }
+  static __device__ inline Cplx<float> get(T t) { return t; }
+};
+template <>
+struct RStore<true> {
+  using T = __nv_bfloat162;
+  static __device__ inline T put(Cplx<float> z) { return __floats2bfloat162_rn(z.re, z.im); }
+  static __device__ inline Cplx<float> get(T t) {
+    float2 f = __bfloat1622float2(t);
+    return cmk(f.x, f.y);
+  }
+};
+template <bool BF>
+__device__ inline Spinor<float> rs_load(const typename RStore<BF>::T* r_s, int vb, int l) {
+  Spinor<float> o;
+#pragma unroll
+  for (int k = 0; k < 12; k++) o.c[k] = RStore<BF>::get(r_s[k * vb + l]);
+  return o;
+}
+template <bool BF>
+__device__ inline void rs_store(typename RStore<BF>::T* r_s, int vb, int l, const Spinor<float>& v) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) r_s[k * vb + l] = RStore<BF>::put(v.c[k]);
+}
+
 // the full 3x3 link (staged with its third row already reconstructed)
 template <typename S>
 __device__ inline SU3<float> smem_link(const typename Stage<S>::C* lk, int vb, int mu, int l) {
@@ -272,22 +307,23 @@ __device__ inline Spinor<float> smem_clover_apply(const typename Stage<S>::W* cl
   return o;
 }
 
-template <typename S, int MU>
-__device__ inline void smem_block_hop(Spinor<float>& p, const Cplx<float>* r_s, const typename Stage<S>::C* lk,
-                                      const SapGeom& sg, int l, const int lc[4], float scale) {
+template <typename S, bool BF, int MU>
+__device__ inline void smem_block_hop(Spinor<float>& p, const typename RStore<BF>::T* r_s,
+                                      const typename Stage<S>::C* lk, const SapGeom& sg, int l, const int lc[4],
+                                      float scale) {
   if (lc[MU] < sg.b[MU] - 1) {
-    HalfSpinor<float> h = project<MU, -1>(smem_load(r_s, sg.vb, l + sg.lst[MU]));
+    HalfSpinor<float> h = project<MU, -1>(rs_load<BF>(r_s, sg.vb, l + sg.lst[MU]));
     h = su3_mul(smem_link<S>(lk, sg.vb, MU, l), h);
     accum_recon<MU, -1>(p, h, scale);
   }
   if (lc[MU] > 0) {
-    HalfSpinor<float> h = project<MU, +1>(smem_load(r_s, sg.vb, l - sg.lst[MU]));
+    HalfSpinor<float> h = project<MU, +1>(rs_load<BF>(r_s, sg.vb, l - sg.lst[MU]));
     h = su3_dag_mul(smem_link<S>(lk, sg.vb, MU, l - sg.lst[MU]), h);
     accum_recon<MU, +1>(p, h, scale);
   }
 }
 
-template <typename S, int MAXT, int MINB>
+template <typename S, bool BF, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_sap_sweep_smem(char* __restrict__ rho, char* __restrict__ psi, char* __restrict__ delta,
                      const float4* __restrict__ gauge, const float4* __restrict__ clover, Geom g, SapGeom sg,
@@ -296,8 +332,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
   using CW = typename Stage<S>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int vb = sg.vb;
-  Cplx<float>* r_s = (Cplx<float>*)smem_raw;
-  CW* lk_s = (CW*)(smem_raw + (size_t)12 * vb * sizeof(Cplx<float>));     // [4][9][vb]
+  using RT = typename RStore<BF>::T;
+  RT* r_s = (RT*)smem_raw;
+  CW* lk_s = (CW*)(smem_raw + (size_t)12 * vb * sizeof(RT));              // [4][9][vb]
   W* cl_s = (W*)(lk_s + (size_t)36 * vb);                                 // [18][vb]
   __shared__ float red[3][32];
 
@@ -349,7 +386,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     face_hop<FieldsF, 2>(r, delta, sg, gauge, g, s, c, lc, kappa);
     face_hop<FieldsF, 3>(r, delta, sg, gauge, g, s, c, lc, kappa);
   }
-  smem_store(r_s, vb, l, r);
+  rs_store<BF>(r_s, vb, l, r);
 
   Spinor<float> x;
 #pragma unroll
@@ -359,10 +396,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
   for (int step = 0; step < nmr; step++) {
     __syncthreads();
     Spinor<float> p = smem_clover_apply<S>(cl_s, vb, l, r);
-    smem_block_hop<S, 0>(p, r_s, lk_s, sg, l, lc, -kappa);
-    smem_block_hop<S, 1>(p, r_s, lk_s, sg, l, lc, -kappa);
-    smem_block_hop<S, 2>(p, r_s, lk_s, sg, l, lc, -kappa);
-    smem_block_hop<S, 3>(p, r_s, lk_s, sg, l, lc, -kappa);
+    smem_block_hop<S, BF, 0>(p, r_s, lk_s, sg, l, lc, -kappa);
+    smem_block_hop<S, BF, 1>(p, r_s, lk_s, sg, l, lc, -kappa);
+    smem_block_hop<S, BF, 2>(p, r_s, lk_s, sg, l, lc, -kappa);
+    smem_block_hop<S, BF, 3>(p, r_s, lk_s, sg, l, lc, -kappa);
     float pr_re = 0, pr_im = 0, pp = 0;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -392,7 +429,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
       r.c[k] = r.c[k] - alpha * p.c[k];
     }
     __syncthreads();
-    smem_store(r_s, vb, l, r);
+    rs_store<BF>(r_s, vb, l, r);
   }
 
   if (psi_init) {
@@ -432,29 +469,37 @@ qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const vo
                              : k_sap_sweep<F, 1024, 1>;
   QCD_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(nblocks / 2, nrhs);
-  // Algorithmic cost of one half-cycle per active site and RHS: rho read and
-  // written, psi read and written (written only in the first cycle), delta
-  // written, the neighbouring blocks' delta read once per face hop, the
-  // site's 4 links and clover term; per MR step the block operator (its
-  // internal hops and the clover term) plus the MR update (24 complex
+  // Algorithmic cost of one half-cycle (the minimum each launch must move):
+  // per active site and RHS, rho read and written, psi read and written (only
+  // written in the first cycle), delta written, and the other colour's delta
+  // read once for every site that lies on a block face (fraction f_face of
+  // the sites); per active site, once per launch, its 4 links and its clover
+  // term.  Flops per active site and RHS: per MR step the block operator
+  // (its internal hops and the clover term) plus the MR update (24 complex
   // multiply-adds), and one hop per face direction for the gather.
-  double face = 0;
-  for (int mu = 0; mu < 4; mu++) face += 2.0 / sg.b[mu];
+  double face = 0, inner = 1;
+  for (int mu = 0; mu < 4; mu++) {
+    face += 2.0 / sg.b[mu];
+    inner *= 1.0 - 2.0 / sg.b[mu];
+  }
+  const double f_face = 1.0 - (inner > 0 ? inner : 0.0);
   const double sb = (double)F::spinor_bytes, lb = (double)F::link_bytes, cb = (double)F::clover_bytes;
   const double half = c->g.V / 2.0;
   const double flops_site = P.nmr * (1320.0 * (1.0 - face / 8.0) + 504.0 + 192.0) + 165.0 * face;
   const int fam = sizeof(typename F::R) == 8 ? FAM_SAP_D : FAM_SAP_F;
   // FP32 with blocks of at most 256 sites: the shared-memory-resident kernel
   const bool resident = sizeof(typename F::R) == 4 && sg.vb <= 256;
-  auto kres = P.sap_half ? k_sap_sweep_smem<__half, 256, 2> : k_sap_sweep_smem<float, 256, 1>;
-  const size_t smem_res = (size_t)sg.vb * (96 + (P.sap_half ? 144 + 144 : 288 + 288));
+  auto kres = P.sap_half == 2   ? k_sap_sweep_smem<__half, true, 256, 2>
+              : P.sap_half == 1 ? k_sap_sweep_smem<__half, false, 256, 2>
+                                : k_sap_sweep_smem<float, false, 256, 1>;
+  const size_t smem_res = (size_t)sg.vb * ((P.sap_half == 2 ? 48 : 96) + (P.sap_half ? 144 + 144 : 288 + 288));
   if (resident)
     QCD_CUDA_OK(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res));
   for (int cy = 0; cy < P.ncy; cy++)
     for (int col = 0; col < 2; col++) {
       const int first = cy == 0 && !accumulate;
-      const double bytes_site = sb * (2 + (first ? 1 : 2) + 1 + face) + 4 * lb + cb;
-      ProfScope ps(c, fam, half * nactive * bytes_site, half * nactive * flops_site);
+      const double bytes_rhs = sb * (2 + (first ? 1 : 2) + 1 + f_face);
+      ProfScope ps(c, fam, half * (nactive * bytes_rhs + 4 * lb + cb), half * nactive * flops_site);
       if (resident)
         kres<<<grid, sg.vb, smem_res, c->stream>>>(rho, psi, delta, (const float4*)gauge, (const float4*)clover, c->g,
                                                    sg, col, !(cy == 0 && col == 0), first, (float)c->kappa, P.nmr,

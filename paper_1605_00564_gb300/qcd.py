@@ -29,7 +29,7 @@ EXPORTS = (
     "qcd_default_params", "qcd_set_params", "qcd_apply_dirac", "qcd_apply_sap", "qcd_solve",
     "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_get_clover", "qcd_profile_enable", "qcd_profile_read",
     "qcd_deflation_setup", "qcd_deflation_fields", "qcd_deflation_little_matrix", "qcd_deflation_little",
-    "qcd_nucleon_2pt_noalloc",
+    "qcd_nucleon_2pt_noalloc", "qcd_autotune", "qcd_fh_forward", "qcd_fh_gradient", "qcd_solve_multi",
 )
 
 
@@ -94,6 +94,11 @@ def load_library(path=LIB_PATH):
     L.qcd_ama_nucleon_2pt.argtypes = [vp, ip, i, i, d, d, dp, dp, ctypes.POINTER(RhsStats)]
     L.qcd_get_clover.argtypes = [vp, vp]
     L.qcd_nucleon_2pt_noalloc.argtypes = [ip, i, vp, ip, vp, i, vp]
+    L.qcd_autotune.argtypes = [vp, vp, i, d, ctypes.c_char_p, ctypes.POINTER(SolverParams)]
+    L.qcd_fh_forward.argtypes = [vp, ip, d, vp, dp, ctypes.POINTER(RhsStats)]
+    L.qcd_solve_multi.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp), ip,
+                                  ctypes.POINTER(dp), ctypes.POINTER(ctypes.POINTER(RhsStats))]
+    L.qcd_fh_gradient.argtypes = [vp, vp, ip, dp, d, dp, ctypes.POINTER(RhsStats)]
     L.qcd_deflation_setup.argtypes = [vp, vp, i, i]
     L.qcd_deflation_fields.argtypes = [vp, vp]
     L.qcd_deflation_little_matrix.argtypes = [vp, dp]
@@ -212,6 +217,16 @@ class Lattice:
         _check(_lib.qcd_apply_sap(self._ctx, _dev_ptr(eta), _dev_ptr(out), n, PREC[precision]))
         return out
 
+    def autotune(self, eta, tol, cache_path=None):
+        """Pick SAP block shape, block-copy precision, nkv and rhs_tile by timing solves of eta."""
+        eta = eta.contiguous()
+        n = eta.shape[0] if eta.dim() == 7 else 1
+        best = SolverParams()
+        cp = cache_path.encode() if cache_path else None
+        _check(_lib.qcd_autotune(self._ctx, _dev_ptr(eta), n, float(tol), cp, ctypes.byref(best)))
+        self.params = best
+        return {"block": list(best.block), "sap_half": best.sap_half, "nkv": best.nkv, "rhs_tile": best.rhs_tile}
+
     def solve(self, eta, tol, psi0=None, allow_not_converged=False):
         """Solve D psi = eta; returns (psi, [stats dict per RHS])."""
         import torch
@@ -292,9 +307,84 @@ class Lattice:
                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, int(mode), int(m)))
         return out[..., 0] + 1j * out[..., 1]
 
+    # ----------------------------------------------------------------------
+    def fh_forward(self, src, tol):
+        """(S in Wilson normalisation [CUDA, 12 spinors], C as numpy float64 [2, T, 2])."""
+        import torch
+        prop = torch.empty(self.spinor_shape(12), dtype=torch.complex128, device="cuda")
+        corr = np.zeros((2, self.T, 2))
+        stats = (RhsStats * 12)()
+        _check(_lib.qcd_fh_forward(self._ctx, (ctypes.c_int * 4)(*src), float(tol), _dev_ptr(prop),
+                                   corr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats))
+        return prop, corr
+
+    def fh_gradient(self, prop, src, gcorr, tol):
+        """(dL/dm0, dL/dlambda) for the upstream gradient gcorr [2, T, 2] of C."""
+        g = np.ascontiguousarray(gcorr, dtype=np.float64)
+        grad = np.zeros(2)
+        stats = (RhsStats * 24)()
+        _check(_lib.qcd_fh_gradient(self._ctx, _dev_ptr(prop.contiguous()), (ctypes.c_int * 4)(*src),
+                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol),
+                                    grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats))
+        return float(grad[0]), float(grad[1])
+
     def get_clover(self):
         """A(x) as a CUDA complex128 tensor [V, 2, 6, 6]."""
         import torch
         out = torch.empty((self.V, 2, 6, 6), dtype=torch.complex128, device="cuda")
         _check(_lib.qcd_get_clover(self._ctx, _dev_ptr(out)))
         return out
+
+
+def solve_multi(lattices, etas, tol):
+    """Solve D psi = eta on several lattices in one call (their kernels overlap
+    on the GPU); every lattice needs its own non-default stream."""
+    import torch
+    L = load_library()
+    n = len(lattices)
+    etas = [e.contiguous() for e in etas]
+    psis = [torch.zeros_like(e) for e in etas]
+    nr = [e.shape[0] if e.dim() == 7 else 1 for e in etas]
+    tols = [(ctypes.c_double * k)(*([float(tol)] * k)) for k in nr]
+    stats = [(RhsStats * k)() for k in nr]
+    VP = ctypes.c_void_p
+    st = L.qcd_solve_multi((VP * n)(*[l._ctx for l in lattices]), n, (VP * n)(*[e.data_ptr() for e in etas]),
+                           (VP * n)(*[p.data_ptr() for p in psis]), (ctypes.c_int * n)(*nr),
+                           (ctypes.POINTER(ctypes.c_double) * n)(*[ctypes.cast(t, ctypes.POINTER(ctypes.c_double)) for t in tols]),
+                           (ctypes.POINTER(RhsStats) * n)(*[ctypes.cast(s, ctypes.POINTER(RhsStats)) for s in stats]))
+    _check(st)
+    return psis, [[s.as_dict() for s in ss] for ss in stats]
+
+
+def _nucleon_fh_class():
+    import torch
+
+    class NucleonFH(torch.autograd.Function):
+        """Point-source nucleon two-point function C (float64 [2, T, 2]: parity,
+        time, re/im) as a function of the bare mass m0 and the axial
+        Feynman-Hellmann coupling lambda (at lambda = 0).  forward: 12 solves and
+        the contraction; backward: the adjoint (gamma_5) solves, all in the
+        library."""
+
+        @staticmethod
+        def forward(ctx, m0, lam, lattice, U, csw, src, tol):
+            if float(lam) != 0.0:
+                raise ValueError("the derivative is taken at lambda = 0")
+            kappa = 1.0 / (2.0 * float(m0) + 8.0)
+            lattice.load_gauge(U, csw, kappa, lattice.time_bc)
+            prop, corr = lattice.fh_forward(src, tol)
+            ctx.lattice, ctx.prop, ctx.src, ctx.tol = lattice, prop, tuple(src), tol
+            return torch.from_numpy(corr)
+
+        @staticmethod
+        def backward(ctx, g):
+            dm, dl = ctx.lattice.fh_gradient(ctx.prop, ctx.src, g.detach().cpu().numpy(), ctx.tol)
+            return (torch.tensor(dm, dtype=torch.float64), torch.tensor(dl, dtype=torch.float64),
+                    None, None, None, None, None)
+
+    return NucleonFH
+
+
+def nucleon_fh(m0, lam, lattice, U, csw, src, tol=1e-12):
+    """Differentiable C(m0, lambda) (see NucleonFH)."""
+    return _nucleon_fh_class().apply(m0, lam, lattice, U, csw, src, tol)

@@ -105,14 +105,23 @@ def test_little_solve(small):
         assert r < 1e-3
 
 
-@pytest.mark.parametrize("half", [0, 1])
-def test_deflated_solve(small, half):
+@pytest.mark.parametrize("half,gen", [(0, 0), (1, 0), (1, 4)])
+def test_deflated_solve(small, half, gen):
+    """gen > 0: subspace rounds after the first use gen iterations of the deflated solver."""
     lat, op, _ = small
-    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=half, dfl=0)
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=half, dfl=0,
+                   dfl_gen_iters=gen)
     src = synth.point_sources(lat.dims, (0, 0, 0, 0))
     eta = to_dev(src)
     _, st0 = lat.solve(eta, 1e-10)
     lat.deflation_setup(to_dev(synth.random_spinor(lat.dims, 56, nrhs=8)), 3)
+    phi = to_host(lat.deflation_fields())
+    from oracle.deflation import Deflation
+    d = Deflation(op, (4, 4, 4, 4))
+    for k in range(8):               # block orthonormal whatever the generation scheme
+        for l in range(8):
+            g = d.block_inner(phi[k], phi[l])
+            assert np.abs(g - (1.0 if k == l else 0.0)).max() < 1e-5
     lat.set_params(dfl=1, dfl_little_iters=16)
     psi, st = lat.solve(eta, 1e-10)
     psi = to_host(psi)
