@@ -323,11 +323,22 @@ __device__ inline void smem_block_hop(Spinor<float>& p, const typename RStore<BF
   }
 }
 
-template <typename S, bool BF, int MAXT, int MINB>
+// B4 = true: the block is 4^4, known at compile time, so every shared-memory
+// offset (component stride vb, neighbour strides) is an immediate.
+template <typename S, bool BF, bool B4, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_sap_sweep_smem(char* __restrict__ rho, char* __restrict__ psi, char* __restrict__ delta,
-                     const float4* __restrict__ gauge, const float4* __restrict__ clover, Geom g, SapGeom sg,
+                     const float4* __restrict__ gauge, const float4* __restrict__ clover, Geom g, SapGeom sg_in,
                      int colour, int gather, int psi_init, float kappa, int nmr, int nrhs, const int* mask) {
+  SapGeom sg = sg_in;
+  if (B4) {
+    sg.b[0] = sg.b[1] = sg.b[2] = sg.b[3] = 4;
+    sg.lst[1] = 1;
+    sg.lst[2] = 4;
+    sg.lst[3] = 16;
+    sg.lst[0] = 64;
+    sg.vb = 256;
+  }
   using W = typename Stage<S>::W;
   using CW = typename Stage<S>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -489,9 +500,12 @@ qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const vo
   const int fam = sizeof(typename F::R) == 8 ? FAM_SAP_D : FAM_SAP_F;
   // FP32 with blocks of at most 256 sites: the shared-memory-resident kernel
   const bool resident = sizeof(typename F::R) == 4 && sg.vb <= 256;
-  auto kres = P.sap_half == 2   ? k_sap_sweep_smem<__half, true, 256, 2>
-              : P.sap_half == 1 ? k_sap_sweep_smem<__half, false, 256, 2>
-                                : k_sap_sweep_smem<float, false, 256, 1>;
+  const bool b4 = sg.b[0] == 4 && sg.b[1] == 4 && sg.b[2] == 4 && sg.b[3] == 4;
+  auto kres = P.sap_half == 2   ? (b4 ? k_sap_sweep_smem<__half, true, true, 256, 2> : k_sap_sweep_smem<__half, true, false, 256, 2>)
+              : P.sap_half == 1 ? (b4 ? k_sap_sweep_smem<__half, false, true, 256, 2>
+                                      : k_sap_sweep_smem<__half, false, false, 256, 2>)
+                                : (b4 ? k_sap_sweep_smem<float, false, true, 256, 1>
+                                      : k_sap_sweep_smem<float, false, false, 256, 1>);
   const size_t smem_res = (size_t)sg.vb * ((P.sap_half == 2 ? 48 : 96) + (P.sap_half ? 144 + 144 : 288 + 288));
   if (resident)
     QCD_CUDA_OK(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res));
