@@ -61,7 +61,8 @@ def config_json(cfg):
         "lattice": [T, X, Y, Z], "kappa": cfg["kappa"], "kappa_named": WORKLOAD["kappa_named"],
         "kappa_note": "at kappa 0.1360 this synthetic field needs ~600 outer iterations (exact) instead of O(100); "
                       "kappa lowered to 0.1300 (~150)", "csw": cfg["csw"], "gauge": "U=exp(i*%g*H) seeded" % cfg["eps"],
-        "solver": "FGCR(nkv=%d, restart_drop=%g) + SAP(block %s, ncy=%d, nmr=%d, FP32, %s block copies)" % (
+        "solver": "FGCR(nkv=%d, restart_drop=%g) + SAP(block %s, ncy=%d, nmr=%d, FP32, %s block copies, CUDA graphs); "
+                  "exact solves start from the sloppy solution" % (
             WORKLOAD["nkv"], WORKLOAD["restart_drop"], "x".join(map(str, WORKLOAD["block"])), WORKLOAD["ncy"],
             WORKLOAD["nmr"], "FP16" if WORKLOAD["sap_half"] else "FP32"),
         "rhs_per_step": 12 * (WORKLOAD["n_g"] + WORKLOAD["n_org"]),
@@ -176,13 +177,23 @@ def oracle_sample(budget_s=20.0):
 
 # ---------------------------------------------------------------------------
 def dist_init():
+    """(world size, rank, local rank); joins the process group when launched by
+    torchrun (NCCL with GPUs, gloo otherwise).  The group carries only the
+    barrier and the max-over-ranks timing: each rank's data stay on its GPU."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
+
+
+def rank_seed(base_seed, rank):
+    """Each rank measures its own gauge configuration (independent problems)."""
+    return int(base_seed) + int(rank)
 
 
 def max_over_ranks(x, ws):
@@ -190,7 +201,8 @@ def max_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -221,9 +233,9 @@ def run_ours(args):
     ws, rank, local = dist_init()
     torch.cuda.set_device(local)
     cfg, srcs = workload_config()
-    seed = cfg["seed"] + rank                 # each rank: its own configuration
+    seed = rank_seed(cfg["seed"], rank)       # each rank: its own configuration
     U = synth.gauge_field(cfg["dims"], cfg["eps"], seed)
-    lat = Lattice(cfg["dims"])
+    lat = Lattice(cfg["dims"], stream=torch.cuda.Stream())   # own stream: SAP applications replay CUDA graphs
     lat.load_gauge(U, cfg["csw"], cfg["kappa"], -1)
     lat.set_params(block=WORKLOAD["block"], ncy=WORKLOAD["ncy"], nmr=WORKLOAD["nmr"], nkv=WORKLOAD["nkv"],
                    precision="f32", sap_half=WORKLOAD["sap_half"], restart_drop=WORKLOAD["restart_drop"],
@@ -276,6 +288,7 @@ def run_ours(args):
     dsl = {}
     for n in (1, 12):
         psi = torch.randn(lat.spinor_shape(n), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
         lat.apply_dirac(psi, precision="f32")
         lat.profile(True)
         for _ in range(10):

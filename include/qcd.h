@@ -80,6 +80,10 @@ typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
  *               deflation; the deflation blocks are the SAP blocks.
  *   dfl_little_iters  steps of the block-Jacobi preconditioned GCR that
  *               approximates A^-1 on the little vectors.
+ *   graphs      1 = each SAP application (its 2 n_cy sweep launches) is replayed
+ *               from a CUDA graph captured on first use for the same buffers
+ *               and parameters (needs a non-default stream; otherwise, and with
+ *               0, the launches are issued one by one).
  *   dfl_gen_iters  subspace generation: 0 = every inverse-iteration round
  *               applies M_SAP; k > 0 = the first round applies M_SAP and the
  *               later rounds k iterations of the deflated SAP-GCR solver.
@@ -103,6 +107,7 @@ typedef struct {
   int dfl;
   int dfl_little_iters;
   int dfl_gen_iters;
+  int graphs;
 } qcd_solver_params;
 
 /* Per right-hand-side outcome of a solve. */
@@ -133,7 +138,7 @@ qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int U_on_device, double
 
 /* Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
  * restart_drop 1e-5, precision F32, rhs_tile 0, sap_half 0, dfl 1,
- * dfl_little_iters 16, dfl_gen_iters 0. */
+ * dfl_little_iters 16, dfl_gen_iters 0, graphs 1. */
 void qcd_default_params(qcd_solver_params* p);
 qcd_status qcd_set_params(qcd_ctx* ctx, const qcd_solver_params* p);
 
@@ -180,8 +185,11 @@ qcd_status qcd_nucleon_2pt(qcd_ctx* ctx, const double* prop, const int src[4], d
  * For each of n_src source positions src[4*i..] the 12 spin-colour point
  * sources are solved to sloppy_tol; the first n_exact positions are also
  * solved to exact_tol (the bias correction, N_org = n_exact).  Positions must
- * be multiples of the SAP block extents so that the translations map the
- * block decomposition onto itself (Sec. 2.2, end).
+ * be multiples of the SAP block extents, and differ from the first source by
+ * an even number of blocks, so that the translations map each of the SAP
+ * domains Omega and Omega* onto itself (Sec. 2.2, end).  The exact solve of a
+ * source starts from its sloppy solution (its iteration counts in stats are
+ * the additional iterations).
  *   corr_ama  host [2][T][2]          the AMA estimate
  *   corr_all  host [n_src + n_exact][2][T][2] or NULL: sloppy correlators
  *             of every source, then exact correlators of the first n_exact

@@ -55,7 +55,7 @@ void devbuf_free(DevBuf& b) {
 }
 
 ProfScope::ProfScope(qcd_ctx* c_, int fam, double bytes, double flops, int kernels) : c(c_), idx(-1) {
-  if (!c || !c->prof_on) return;
+  if (!c || !c->prof_on || c->prof_suspend) return;
   ProfRec r;
   r.fam = fam;
   r.kernels = kernels;
@@ -121,6 +121,7 @@ qcd_status validate_params(const qcd_ctx* c, const qcd_solver_params* p) {
   ARG_CHECK(p->dfl == 0 || p->dfl == 1, "dfl must be 0 or 1");
   ARG_CHECK(p->dfl_little_iters >= 1 && p->dfl_little_iters <= 64, "dfl_little_iters must be in [1, 64]");
   ARG_CHECK(p->dfl_gen_iters >= 0 && p->dfl_gen_iters <= 64, "dfl_gen_iters must be in [0, 64]");
+  ARG_CHECK(p->graphs == 0 || p->graphs == 1, "graphs must be 0 or 1");
   return QCD_OK;
 }
 
@@ -163,6 +164,7 @@ void qcd_default_params(qcd_solver_params* p) {
   p->dfl = 1;
   p->dfl_little_iters = 16;
   p->dfl_gen_iters = 0;
+  p->graphs = 1;
 }
 
 qcd_status qcd_create(qcd_ctx** out, const int dims[4], void* cuda_stream) {
@@ -211,8 +213,10 @@ void qcd_destroy(qcd_ctx* c) {
   devbuf_free(c->scal);
   devbuf_free(c->contract);
   devbuf_free(c->stage);
+  devbuf_free(c->guess);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   dfl_free(c);
+  for (auto& gph : c->sap_graphs) cudaGraphExecDestroy(gph.exec);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -374,6 +378,14 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* c, const int* src, int n_src, int n_exac
                 "source %d is not a multiple of the SAP block extent in direction %d: the translation would not map "
                 "the block decomposition onto itself", i, mu);
     }
+  // the translations between the sources must map Omega onto Omega (even shift in blocks)
+  for (int i = 1; i < n_src; i++) {
+    int par = 0;
+    for (int mu = 0; mu < 4; mu++) par += (src[4 * i + mu] - src[mu]) / c->params.block[mu];
+    ARG_CHECK((par & 1) == 0,
+              "sources 0 and %d differ by an odd number of blocks: the translation would exchange the SAP domains "
+              "Omega and Omega*", i);
+  }
   const int T = c->g.L[0];
   const int njobs = n_src + n_exact;   // sloppy solves of every source, then exact solves
   std::vector<double> corr((size_t)njobs * 4 * T);
@@ -388,6 +400,14 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* c, const int* src, int n_src, int n_exac
   std::vector<double> tols(12 * spt);
   int* d_sites = nullptr;
   QCD_CUDA_OK(cudaMalloc(&d_sites, sizeof(int) * 12 * spt));
+  DevBuf& guess = c->guess;   // sloppy propagators of the exact-solve sources
+  {
+    qcd_status g = devbuf_ensure(guess, spinor_bytes(c, QCD_PREC_F64) * 12 * n_exact);
+    if (g != QCD_OK) {
+      cudaFree(d_sites);
+      return g;
+    }
+  }
   qcd_status rc = QCD_OK;
   for (int j0 = 0; j0 < njobs && rc == QCD_OK; j0 += spt) {
     // jobs of one tile share a tolerance: do not mix sloppy and exact
@@ -412,11 +432,30 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* c, const int* src, int n_src, int n_exac
       qcd_set_error("source set-up failed");
       break;
     }
+    // the exact solve of a source starts from that source's sloppy solution
+    const size_t prop_bytes = spinor_bytes(c, QCD_PREC_F64) * 12;
+    if (j0 >= n_src)
+      for (int k = 0; k < nj; k++)
+        if (cudaMemcpyAsync((char*)c->wsD[1].p + prop_bytes * k, (const char*)guess.p + prop_bytes * (j0 + k - n_src),
+                            prop_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+          rc = QCD_ERR_CUDA;
+          qcd_set_error("initial guess copy failed");
+        }
+    if (rc != QCD_OK) break;
     {
       ProfScope ps(c, FAM_LAYOUT, 0.0, 0.0);
       k_point_sources<<<(n + 63) / 64, 64, 0, c->stream>>>((double2*)c->wsD[0].p, d_sites, c->g.V, n);
     }
     rc = solver_run(c, n, tols.data(), st.data() + (size_t)12 * j0);
+    if (rc != QCD_OK) break;
+    if (j0 < n_src)
+      for (int k = 0; k < nj; k++)
+        if (j0 + k < n_exact &&
+            cudaMemcpyAsync((char*)guess.p + prop_bytes * (j0 + k), (const char*)c->wsD[1].p + prop_bytes * k,
+                            prop_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+          rc = QCD_ERR_CUDA;
+          qcd_set_error("initial guess copy failed");
+        }
     if (rc != QCD_OK) break;
     for (int k = 0; k < nj && rc == QCD_OK; k++) {
       int si = (j0 + k) < n_src ? (j0 + k) : (j0 + k - n_src);

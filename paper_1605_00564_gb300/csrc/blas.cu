@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth(char* __restrict__ chi, size
 // Site-major form of k_gs_orth: a thread holds all 12 components of chi_k
 // for its site and walks the j < k vectors with independent loads (the j
 // loop is unrolled to KMAX), so many loads are in flight per thread.
-template <typename X, int KMAX>
+template <typename X, typename RH, int KMAX>
 __global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, size_t jstride, int k,
                                                         const double2* __restrict__ dots, const char* __restrict__ rho,
                                                         int V, int nrhs, double2* __restrict__ part, const int* mask) {
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, s
   __syncthreads();
   const size_t roff = (size_t)rhs * X::bytes * V;
   char* ckp = chi + k * jstride + roff;
-  const char* rp = rho + (size_t)rhs * PD::bytes * V;
+  const char* rp = rho + (size_t)rhs * RH::bytes * V;
   double n2 = 0, cr = 0, ci = 0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
     Cplx<R> a[12];
@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, s
     for (int q = 0; q < 6; q++) X::st(ckp, V, q, s, a[2 * q], a[2 * q + 1]);
 #pragma unroll
     for (int q = 0; q < 6; q++) {
-      Cplx<double> x, y;
-      PD::ld(rp, V, q, s, x, y);
+      Cplx<typename RH::R> x, y;
+      RH::ld(rp, V, q, s, x, y);
       const Cplx<R> p0 = a[2 * q], p1 = a[2 * q + 1];
       n2 += (double)(p0.re * p0.re + p0.im * p0.im + p1.re * p1.re + p1.im * p1.im);
       cr += (double)p0.re * x.re + (double)p0.im * x.im + (double)p1.re * y.re + (double)p1.im * y.im;
@@ -496,6 +496,42 @@ __global__ void __launch_bounds__(GS_TPB) k_caxpy_sm(char* __restrict__ y, const
 #pragma unroll
     for (int q = 0; q < 6; q++) PD::st(yb, V, q, s, a[2 * q], a[2 * q + 1]);
   }
+}
+
+// chi_k *= inv; rho -= ck * chi_k with rho in the inner precision X; partial |rho|^2
+template <typename X>
+__global__ void __launch_bounds__(GS_TPB) k_gs_finish_inner(char* __restrict__ chik, const double* __restrict__ inv,
+                                                             const double2* __restrict__ ck, char* __restrict__ rho,
+                                                             int V, double2* __restrict__ part, const int* mask) {
+  __shared__ double sh[32];
+  const int rhs = blockIdx.y;
+  if (mask && !mask[rhs]) return;
+  using R = typename X::R;
+  char* cp = chik + (size_t)rhs * X::bytes * V;
+  char* rp = rho + (size_t)rhs * X::bytes * V;
+  const R f = (R)inv[rhs];
+  const Cplx<R> c = cmk((R)ck[rhs].x, (R)ck[rhs].y);
+  double n2 = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+    R acc = 0;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      Cplx<R> a, b, x, y;
+      X::ld(cp, V, q, s, a, b);
+      X::ld(rp, V, q, s, x, y);
+      a = f * a;
+      b = f * b;
+      x = x - c * a;
+      y = y - c * b;
+      X::st(cp, V, q, s, a, b);
+      X::st(rp, V, q, s, x, y);
+      acc += x.re * x.re + x.im * x.im + y.re * y.re + y.im * y.im;
+    }
+    n2 += (double)acc;
+  }
+  double v[1] = {n2};
+  block_sum_n<1>(v, sh);
+  if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = make_double2(v[0], 0.0);
 }
 
 // chi_k *= inv; rho -= ck * chi_k; rho_s = rho in the inner precision; partial |rho|^2
@@ -650,12 +686,12 @@ qcd_status blas_gs_dots(qcd_ctx* c, const void* chi, int prec, size_t jstride, i
 
 // chi_k -= sum_j dots[j] chi_j; n2c[0][r] = |chi_k|^2 (re), n2c[1][r] = (chi_k, rho)
 qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, const double* dots_dev,
-                        const void* rho, int nrhs, double* n2c_dev, const int* mask, int nactive) {
+                        const void* rho, int prho, int nrhs, double* n2c_dev, const int* mask, int nactive) {
   const int G = red_grid(c);
   QCD_TRY(devbuf_ensure(c->red, (size_t)G * 2 * nrhs * sizeof(double2)));
   const double vb = prec == QCD_PREC_F64 ? 192 : 96;
-  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * ((k + 2) * vb + 192), (double)c->g.V * nactive * (k + 2) * 48,
-               2);
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * ((k + 2) * vb + (prho == QCD_PREC_F64 ? 192 : 96)),
+               (double)c->g.V * nactive * (k + 2) * 48, 2);
   const dim3 grid(G, nrhs);
   char* cp = (char*)chi;
   const double2* dp = (const double2*)dots_dev;
@@ -663,12 +699,15 @@ qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, 
   double2* pp = (double2*)c->red.p;
   if (prec == QCD_PREC_F64)
     k_gs_orth<PD><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
-  else if (k <= 8)
-    k_gs_orth_sm<PF, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
-  else if (k <= 16)
-    k_gs_orth_sm<PF, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
-  else
-    k_gs_orth_sm<PF, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+  else if (prho == QCD_PREC_F64) {
+    if (k <= 8) k_gs_orth_sm<PF, PD, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+    else if (k <= 16) k_gs_orth_sm<PF, PD, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+    else k_gs_orth_sm<PF, PD, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+  } else {
+    if (k <= 8) k_gs_orth_sm<PF, PF, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+    else if (k <= 16) k_gs_orth_sm<PF, PF, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+    else k_gs_orth_sm<PF, PF, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+  }
   k_sum_parts<<<dim3(2, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 2, G, (double2*)n2c_dev, nrhs,
                                                         mask);
   QCD_CUDA_OK(cudaGetLastError());
@@ -690,6 +729,25 @@ qcd_status blas_gs_finish(qcd_ctx* c, void* chik, int prec, const double* inv_de
     k_gs_finish<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
                                                             (char*)rho, (char*)rho_s, c->g.V, (double2*)c->red.p,
                                                             mask);
+  k_sum_parts<<<dim3(1, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 1, G, (double2*)rn2_dev, nrhs,
+                                                        mask);
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
+}
+
+// chi_k *= inv; rho -= ck chi_k with rho in the inner precision; rn2[r] = |rho|^2 (double2 .x)
+qcd_status blas_gs_finish_inner(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev,
+                                void* rho, int nrhs, double* rn2_dev, const int* mask, int nactive) {
+  const int G = red_grid(c);
+  QCD_TRY(devbuf_ensure(c->red, (size_t)G * nrhs * sizeof(double2)));
+  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * 4 * vb, (double)c->g.V * nactive * 96, 2);
+  if (prec == QCD_PREC_F64)
+    k_gs_finish_inner<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
+                                                                  (char*)rho, c->g.V, (double2*)c->red.p, mask);
+  else
+    k_gs_finish_inner<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
+                                                                  (char*)rho, c->g.V, (double2*)c->red.p, mask);
   k_sum_parts<<<dim3(1, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 1, G, (double2*)rn2_dev, nrhs,
                                                         mask);
   QCD_CUDA_OK(cudaGetLastError());

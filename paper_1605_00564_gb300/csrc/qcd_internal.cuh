@@ -320,8 +320,18 @@ struct ProfRec {
   double bytes, flops;
 };
 
+struct SapGraph {
+  const void *rho_src, *rho, *psi, *delta, *gauge, *clover;
+  const int* mask;
+  int nrhs, ncy, nmr, accumulate, half, prec, block[4];
+  double kappa;
+  cudaGraphExec_t exec;
+};
+
 struct qcd_ctx {
   int prof_on = 0;
+  int prof_suspend = 0;          // > 0 while a stream is being captured
+  std::vector<SapGraph> sap_graphs;
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> evpool;
   Geom g;
@@ -341,6 +351,7 @@ struct qcd_ctx {
   DevBuf scal;        // device scalars of the solver
   DevBuf contract;    // per-site contraction values
   DevBuf stage;       // staging for host <-> device copies
+  DevBuf guess;       // sloppy solutions reused as initial guesses of exact solves
   double* host_scal = nullptr;   // pinned mirror of scalars
   size_t host_scal_bytes = 0;
   void* dfl = nullptr;           // deflation state (dfl.cu)
@@ -383,16 +394,20 @@ qcd_status blas_scale(qcd_ctx* c, void* x, int px, const double* sc_dev, int nrh
 qcd_status blas_gs_dots(qcd_ctx* c, const void* chi, int prec, size_t jstride, int k, int nrhs, double* dots_dev,
                         const int* mask, int nactive);
 qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, const double* dots_dev,
-                        const void* rho, int nrhs, double* n2c_dev, const int* mask, int nactive);
+                        const void* rho, int prho, int nrhs, double* n2c_dev, const int* mask, int nactive);
+// chi_k *= inv; rho -= ck chi_k, rho in the inner precision prec
+qcd_status blas_gs_finish_inner(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev,
+                                void* rho, int nrhs, double* rn2_dev, const int* mask, int nactive);
 qcd_status blas_gs_finish(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev, void* rho,
                           void* rho_s, int nrhs, double* rn2_dev, const int* mask, int nactive);
 // out = x - y
 qcd_status blas_xmy(qcd_ctx* c, const void* x, const void* y, void* out, int prec, int nrhs, const int* mask);
 
 // SAP preconditioner: psi = M_SAP rho (rho is overwritten), precision prec
-// accumulate != 0: psi += M_SAP rho instead of psi = M_SAP rho
+// psi = M_SAP rho_src (accumulate != 0: psi += M_SAP rho_src); rho is the SAP's
+// working residual (overwritten); rho_src = nullptr means rho itself
 qcd_status sap_apply(qcd_ctx* c, void* rho, void* psi, void* delta, int prec, int nrhs, const int* mask,
-                     int nactive, int accumulate = 0);
+                     int nactive, int accumulate = 0, const void* rho_src = nullptr);
 
 // deflation (dfl.cu)
 qcd_status dfl_setup(qcd_ctx* c, const double* init_dev, int ns, int n_inv);

@@ -20,6 +20,8 @@
 // One CTA per block and right-hand side, one thread per block site; the
 // block's residual lives in shared memory across the MR steps, the solution
 // increment x in registers.
+#include <string.h>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -94,7 +96,8 @@ __device__ inline R warp_sum(R v) {
 }
 
 template <typename F, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(char* __restrict__ rho, char* __restrict__ psi, char* __restrict__ delta,
+__global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(const char* __restrict__ rho_src, char* __restrict__ rho,
+                                                          char* __restrict__ psi, char* __restrict__ delta,
                             const void* __restrict__ gauge, const void* __restrict__ clover, Geom g, SapGeom sg,
                             int colour, int gather, int psi_init, typename F::R kappa, int nmr, int nrhs,
                             const int* mask) {
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(char* __restrict__ rho
   const int rhs = blockIdx.y;
   if (mask && !mask[rhs]) return;
   const size_t off = (size_t)rhs * F::spinor_bytes * g.V;
+  rho_src += off;
   rho += off;
   psi += off;
   delta += off;
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(char* __restrict__ rho
   const int s = ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
 
   // pending boundary update from the previous half-cycle
-  Spinor<R> r = F::load_spinor(rho, g.V, s);
+  Spinor<R> r = F::load_spinor(rho_src, g.V, s);
   if (gather) {
     face_hop<F, 0>(r, delta, sg, gauge, g, s, c, lc, kappa);
     face_hop<F, 1>(r, delta, sg, gauge, g, s, c, lc, kappa);
@@ -327,7 +331,8 @@ __device__ inline void smem_block_hop(Spinor<float>& p, const typename RStore<BF
 // offset (component stride vb, neighbour strides) is an immediate.
 template <typename S, bool BF, bool B4, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
-    k_sap_sweep_smem(char* __restrict__ rho, char* __restrict__ psi, char* __restrict__ delta,
+    k_sap_sweep_smem(const char* __restrict__ rho_src, char* __restrict__ rho, char* __restrict__ psi,
+                     char* __restrict__ delta,
                      const float4* __restrict__ gauge, const float4* __restrict__ clover, Geom g, SapGeom sg_in,
                      int colour, int gather, int psi_init, float kappa, int nmr, int nrhs, const int* mask) {
   SapGeom sg = sg_in;
@@ -352,6 +357,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
   const int rhs = blockIdx.y;
   if (mask && !mask[rhs]) return;
   const size_t off = (size_t)rhs * FieldsF::spinor_bytes * g.V;
+  rho_src += off;
   rho += off;
   psi += off;
   delta += off;
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
 #pragma unroll
   for (int k = 0; k < 18; k++) cl_s[(size_t)k * vb + l] = Stage<S>::put(__ldg(clover + (size_t)k * g.V + s));
 
-  Spinor<float> r = FieldsF::load_spinor(rho, g.V, s);
+  Spinor<float> r = FieldsF::load_spinor(rho_src, g.V, s);
   if (gather) {
     face_hop<FieldsF, 0>(r, delta, sg, gauge, g, s, c, lc, kappa);
     face_hop<FieldsF, 1>(r, delta, sg, gauge, g, s, c, lc, kappa);
@@ -456,8 +462,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
 }
 
 template <typename F>
-qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const void* gauge, const void* clover,
-                         int nrhs, const int* mask, int nactive, int accumulate) {
+qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, char* delta, const void* gauge,
+                         const void* clover, int nrhs, const int* mask, int nactive, int accumulate) {
   const qcd_solver_params& P = c->params;
   SapGeom sg;
   sg.vb = 1;
@@ -509,30 +515,81 @@ qcd_status launch_sweeps(qcd_ctx* c, char* rho, char* psi, char* delta, const vo
   const size_t smem_res = (size_t)sg.vb * ((P.sap_half == 2 ? 48 : 96) + (P.sap_half ? 144 + 144 : 288 + 288));
   if (resident)
     QCD_CUDA_OK(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res));
-  for (int cy = 0; cy < P.ncy; cy++)
-    for (int col = 0; col < 2; col++) {
-      const int first = cy == 0 && !accumulate;
-      const double bytes_rhs = sb * (2 + (first ? 1 : 2) + 1 + f_face);
-      ProfScope ps(c, fam, half * (nactive * bytes_rhs + 4 * lb + cb), half * nactive * flops_site);
-      if (resident)
-        kres<<<grid, sg.vb, smem_res, c->stream>>>(rho, psi, delta, (const float4*)gauge, (const float4*)clover, c->g,
-                                                   sg, col, !(cy == 0 && col == 0), first, (float)c->kappa, P.nmr,
-                                                   nrhs, mask);
-      else
-        kern<<<grid, sg.vb, smem, c->stream>>>(rho, psi, delta, gauge, clover, c->g, sg, col, !(cy == 0 && col == 0),
-                                               first, (typename F::R)c->kappa, P.nmr, nrhs, mask);
-      QCD_CUDA_OK(cudaGetLastError());
+  auto issue = [&]() -> qcd_status {
+    for (int cy = 0; cy < P.ncy; cy++)
+      for (int col = 0; col < 2; col++) {
+        const int first = cy == 0 && !accumulate;
+        const double bytes_rhs = sb * (2 + (first ? 1 : 2) + 1 + f_face);
+        ProfScope ps(c, fam, half * (nactive * bytes_rhs + 4 * lb + cb), half * nactive * flops_site);
+        const char* rin = cy == 0 ? rho_src : rho;   // the first cycle reads the caller's residual
+        if (resident)
+          kres<<<grid, sg.vb, smem_res, c->stream>>>(rin, rho, psi, delta, (const float4*)gauge, (const float4*)clover,
+                                                     c->g, sg, col, !(cy == 0 && col == 0), first, (float)c->kappa,
+                                                     P.nmr, nrhs, mask);
+        else
+          kern<<<grid, sg.vb, smem, c->stream>>>(rin, rho, psi, delta, gauge, clover, c->g, sg, col,
+                                                 !(cy == 0 && col == 0), first, (typename F::R)c->kappa, P.nmr, nrhs,
+                                                 mask);
+        QCD_CUDA_OK(cudaGetLastError());
+      }
+    return QCD_OK;
+  };
+  if (!P.graphs || c->stream == nullptr) return issue();
+  // replay the whole application from a cached CUDA graph
+  SapGraph key;
+  key.rho_src = rho_src;
+  key.rho = rho; key.psi = psi; key.delta = delta; key.gauge = gauge; key.clover = clover; key.mask = mask;
+  key.nrhs = nrhs; key.ncy = P.ncy; key.nmr = P.nmr; key.accumulate = accumulate; key.half = P.sap_half;
+  key.prec = (int)sizeof(typename F::R);
+  for (int mu = 0; mu < 4; mu++) key.block[mu] = P.block[mu];
+  key.kappa = c->kappa;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& gph : c->sap_graphs)
+    if (gph.rho_src == key.rho_src && gph.rho == key.rho && gph.psi == key.psi && gph.delta == key.delta && gph.gauge == key.gauge &&
+        gph.clover == key.clover && gph.mask == key.mask && gph.nrhs == key.nrhs && gph.ncy == key.ncy &&
+        gph.nmr == key.nmr && gph.accumulate == key.accumulate && gph.half == key.half && gph.prec == key.prec &&
+        gph.kappa == key.kappa && memcmp(gph.block, key.block, sizeof(key.block)) == 0) {
+      exec = gph.exec;
+      break;
     }
+  if (!exec) {
+    cudaGraph_t graph = nullptr;
+    QCD_CUDA_OK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->prof_suspend++;
+    qcd_status st = issue();
+    c->prof_suspend--;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (st != QCD_OK) return st;
+    QCD_CUDA_OK(e);
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    QCD_CUDA_OK(e);
+    if (c->sap_graphs.size() >= 64) {
+      cudaGraphExecDestroy(c->sap_graphs.front().exec);
+      c->sap_graphs.erase(c->sap_graphs.begin());
+    }
+    key.exec = exec;
+    c->sap_graphs.push_back(key);
+  }
+  double bytes = 0, flops = 0;
+  for (int cy = 0; cy < P.ncy; cy++) {
+    const int first = cy == 0 && !accumulate;
+    bytes += 2 * half * (nactive * sb * (2 + (first ? 1 : 2) + 1 + f_face) + 4 * lb + cb);
+    flops += 2 * half * nactive * flops_site;
+  }
+  ProfScope ps(c, fam, bytes, flops, 2 * P.ncy);
+  QCD_CUDA_OK(cudaGraphLaunch(exec, c->stream));
   return QCD_OK;
 }
 
 }  // namespace
 
 qcd_status sap_apply(qcd_ctx* c, void* rho, void* psi, void* delta, int prec, int nrhs, const int* mask,
-                     int nactive, int accumulate) {
+                     int nactive, int accumulate, const void* rho_src) {
+  const char* src = rho_src ? (const char*)rho_src : (const char*)rho;
   if (prec == QCD_PREC_F64)
-    return launch_sweeps<FieldsD>(c, (char*)rho, (char*)psi, (char*)delta, c->gaugeD.p, c->cloverD.p, nrhs, mask,
-                                  nactive, accumulate);
-  return launch_sweeps<FieldsF>(c, (char*)rho, (char*)psi, (char*)delta, c->gaugeF.p, c->cloverF.p, nrhs, mask,
+    return launch_sweeps<FieldsD>(c, src, (char*)rho, (char*)psi, (char*)delta, c->gaugeD.p, c->cloverD.p, nrhs,
+                                  mask, nactive, accumulate);
+  return launch_sweeps<FieldsF>(c, src, (char*)rho, (char*)psi, (char*)delta, c->gaugeF.p, c->cloverF.p, nrhs, mask,
                                 nactive, accumulate);
 }

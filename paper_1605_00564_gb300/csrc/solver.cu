@@ -41,7 +41,7 @@ __global__ void k_gs_scalars(const double2* n2c, double* b, double* inv, double2
 
 struct Work {
   char *eta, *psi, *rho, *tmp;      // FP64 internal [n]
-  char *rhoS, *delta;               // inner precision [n]
+  char *rhoS, *delta, *sapin;       // inner precision [n]: recursive residual, SAP scratch
   char *phi, *chi;                  // inner precision [nkv][n]
   double2 *a;                       // [nkv][nkv][n]: a[k][j][r]
   double *b, *inv, *rn2;            // [nkv][n], [n], [n]
@@ -65,10 +65,11 @@ qcd_status get_work(qcd_ctx* c, int n, int nkv, int prec, Work& w) {
   w.rho = (char*)bufD[2].p;
   w.tmp = (char*)bufD[3].p;
   DevBuf& basis = prec == QCD_PREC_F64 ? c->basisD : c->basisF;
-  QCD_TRY(devbuf_ensure(basis, VI * (2 * nkv + 2)));
+  QCD_TRY(devbuf_ensure(basis, VI * (2 * nkv + 3)));
   w.rhoS = (char*)basis.p;
   w.delta = w.rhoS + VI;
-  w.phi = w.delta + VI;
+  w.sapin = w.delta + VI;
+  w.phi = w.sapin + VI;
   w.chi = w.phi + VI * nkv;
   size_t sz = align256(sizeof(double2) * nkv * nkv * n) + align256(sizeof(double) * nkv * n) +
               2 * align256(sizeof(double) * n) + 2 * align256(sizeof(double2) * nkv * n) +
@@ -202,29 +203,32 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
       char* phik = w.phi + VI * k;
       char* chik = w.chi + VI * k;
       if (k == 0) QCD_TRY(blas_convert(c, w.rho, QCD_PREC_F64, w.rhoS, prec, n, w.mask));
+      // SAP works in sapin; its first cycle reads the recursive residual rhoS
       if (use_dfl) {
         // deflated preconditioner: phi_k = Phi A^-1 Phi^+ rho + M_SAP(rho - D Phi A^-1 Phi^+ rho)
         QCD_TRY(dfl_low_mode(c, w.rhoS, phik, n, w.mask, nin_now, P.dfl_little_iters));
         QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now));
-        QCD_TRY(blas_xmy(c, w.rhoS, chik, w.rhoS, prec, n, w.mask));
-        QCD_TRY(sap_apply(c, w.rhoS, phik, w.delta, prec, n, w.mask, nin_now, 1));
+        QCD_TRY(blas_xmy(c, w.rhoS, chik, w.sapin, prec, n, w.mask));
+        QCD_TRY(sap_apply(c, w.sapin, phik, w.delta, prec, n, w.mask, nin_now, 1));
       } else {
-        QCD_TRY(sap_apply(c, w.rhoS, phik, w.delta, prec, n, w.mask, nin_now));
+        QCD_TRY(sap_apply(c, w.sapin, phik, w.delta, prec, n, w.mask, nin_now, 0, w.rhoS));
       }
       QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now));
       // Gram-Schmidt against chi_0..chi_{k-1}, normalisation, residual update;
       // the update also writes the next preconditioner input rhoS
       double2* ak = w.a + (size_t)k * nkv * n;
       QCD_TRY(blas_gs_dots(c, w.chi, prec, VI, k, n, (double*)ak, w.mask, nin_now));
-      QCD_TRY(blas_gs_orth(c, w.chi, prec, VI, k, (const double*)ak, w.rho, n, (double*)w.n2c, w.mask, nin_now));
+      // the recursive residual of the cycle is rhoS, in the inner precision
+      QCD_TRY(blas_gs_orth(c, w.chi, prec, VI, k, (const double*)ak, w.rhoS, prec, n, (double*)w.n2c, w.mask,
+                           nin_now));
       {
         ProfScope ps(c, FAM_BLAS, 0.0, 0.0);
         k_gs_scalars<<<(n + 63) / 64, 64, 0, c->stream>>>(w.n2c, w.b + (size_t)k * n, w.inv, w.cc + (size_t)k * n, n,
                                                           w.mask);
       }
       QCD_CUDA_OK(cudaGetLastError());
-      QCD_TRY(blas_gs_finish(c, chik, prec, w.inv, (const double*)(w.cc + (size_t)k * n), w.rho, w.rhoS, n,
-                             (double*)w.rn2c, w.mask, nin_now));
+      QCD_TRY(blas_gs_finish_inner(c, chik, prec, w.inv, (const double*)(w.cc + (size_t)k * n), w.rhoS, n,
+                                   (double*)w.rn2c, w.mask, nin_now));
       QCD_TRY(fetch(c, h_rn2c, w.rn2c, sizeof(double2) * n));
       for (int r = 0; r < n; r++) h_rn2[r] = h_rn2c[r].x;
       kmax = k + 1;

@@ -169,17 +169,25 @@ def random_su3_field(dims, seed):
     return _reunitarise(Q)
 
 
-def ama_source_shifts(dims, n_g):
+def ama_source_shifts(dims, n_g, block=(4, 4, 4, 4)):
     """n_g source positions (t, x, y, z) for the AMA translations.
 
-    The translations must map the SAP block decomposition onto itself, so
-    every component is a multiple of the block extent: t = 8 i mod T and
-    x, y, z alternate between 0 and half the lattice extent (bits 0, 1, 2 of
-    i).  For the lattices used here (L = 8, 24, 32, 48; T = 16, 48, 64, 96)
-    these are multiples of the 4^4, 8x4^3 and 6^4 blocks.
+    The translations must map the SAP domains Omega and Omega* (the black and
+    the white blocks) onto themselves: every component is a multiple of the
+    block extent and the shift measured in blocks has an even sum.  Here each
+    component is a multiple of twice the block extent: t = 2 b_t i mod T and
+    x, y, z alternate between 0 and the largest multiple of 2 b below half the
+    extent (bits 0, 1, 2 of i).  For T = 64, L = 32 and 4^4 blocks this gives
+    t = 8 i and x, y, z in {0, 16}.
     """
     T, X, Y, Z = (int(d) for d in dims)
+    bt, bx, by, bz = (int(b) for b in block)
+
+    def half(L, b):
+        return (L // 2) // (2 * b) * (2 * b)
+
+    hx, hy, hz = half(X, bx), half(Y, by), half(Z, bz)
     out = []
     for i in range(n_g):
-        out.append(((8 * i) % T, (X // 2) * (i & 1), (Y // 2) * ((i >> 1) & 1), (Z // 2) * ((i >> 2) & 1)))
+        out.append(((2 * bt * i) % T, hx * (i & 1), hy * ((i >> 1) & 1), hz * ((i >> 2) & 1)))
     return out

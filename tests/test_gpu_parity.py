@@ -153,3 +153,44 @@ def test_solve_multi_two_lattices():
             assert st[r]["status"] == "QCD_OK"
             assert np.linalg.norm(eh[r] - op.D(ph[r])) / np.linalg.norm(eh[r]) <= 1.1e-10
         lat.close()
+
+
+def test_ama_estimate(small):
+    """qcd_ama_nucleon_2pt: the AMA combination equals eqs. caa1/caa2 (oracle) applied
+    to the returned per-source correlators; the exact correlator equals an independent
+    exact solve + contraction; the sloppy ones track it at the solver tolerance."""
+    from oracle import nucleon
+    lat, op, _ = small
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=1, dfl=0)
+    srcs = synth.ama_source_shifts(lat.dims, 2)
+    ama, allc, st = lat.ama_nucleon_2pt(srcs, 1, 1e-3, 1e-10)
+    assert all(s["status"] == "QCD_OK" for s in st)
+    ref = nucleon.ama_combine(allc[:2], allc[2:3], allc[0:1])
+    assert np.abs(ama - ref).max() <= 1e-14 * np.abs(ref).max()
+    psi, _ = lat.solve(to_dev(synth.point_sources(lat.dims, srcs[0])), 1e-10)
+    c_ex = lat.nucleon_2pt(psi, srcs[0], precision="f64")
+    assert np.abs(allc[2] - c_ex).max() <= 1e-6 * np.abs(c_ex).max()
+    assert np.abs(allc[0] - c_ex)[0, :4].max() <= 5e-2 * np.abs(c_ex[0, :4]).max()
+
+
+def test_sap_cuda_graph_replay(small):
+    """On a non-default stream each SAP application is captured once and replayed
+    from a CUDA graph; replays give the same bits as direct launches."""
+    import torch
+    from paper_1605_00564_gb300.qcd import Lattice
+    _, _, U = small
+    cfg = synth.CONFIGS["small_8c16"]
+    s = torch.cuda.Stream()
+    lg = Lattice(cfg["dims"], stream=s)
+    lg.load_gauge(U, cfg["csw"], cfg["kappa"], -1)
+    eta = to_dev(synth.random_spinor(cfg["dims"], 91, nrhs=2))
+    torch.cuda.synchronize()
+    out = []
+    for graphs in (0, 1, 1):               # direct, capture + replay, replay
+        lg.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, sap_half=1, graphs=graphs)
+        with torch.cuda.stream(s):
+            r = lg.apply_sap(eta)
+        s.synchronize()
+        out.append(to_host(r))
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[1], out[2])
+    lg.close()

@@ -3,10 +3,11 @@
 * batched = single: a right-hand side solved inside a batch gives the same bits as
   solved alone (every kernel and reduction works per RHS in a fixed order);
 * translation covariance of the sloppy correlator (the paper's covariance test,
-  Sec. 3.1): a source shifted by a multiple of the SAP block extent on the
-  correspondingly shifted gauge field gives the same correlator up to rounding
-  (delta_c ~ 1e-7 in FP32), while a shift that does not map the blocks onto
-  themselves changes the sloppy solution at the level of the solver tolerance;
+  Sec. 3.1): a source shifted by a translation that maps each SAP domain onto
+  itself (an even number of blocks), on the correspondingly shifted gauge field,
+  gives the same correlator up to rounding, while a shift that exchanges Omega and
+  Omega* or does not map blocks onto blocks changes the sloppy solution at the
+  level of the solver tolerance;
 * failure paths (made on the host): zero source, NaN source, max_outer = 1,
   invalid arguments.
 """
@@ -53,17 +54,20 @@ def test_translation_covariance_block_preserving():
     cfg = synth.CONFIGS["small_8c16"]
     U = synth.gauge_field(cfg["dims"], cfg["eps"], cfg["seed"])
     c0 = _sloppy_corr(U, (0, 0, 0, 0))
-    g = (4, 4, 0, 4)                                     # multiples of the 4^4 blocks
-    Ug = np.roll(U, shift=(g[0], g[3], g[2], g[1]), axis=(0, 1, 2, 3))
-    cg = _sloppy_corr(Ug, g)
-    delta = np.abs(cg[0] - c0[0]) / np.abs(c0[0])
-    assert delta[:8].max() < 1e-5, delta
-    # a shift by one site breaks the block decomposition's covariance
-    g1 = (1, 0, 0, 0)
-    U1 = np.roll(U, shift=(1, 0, 0, 0), axis=(0, 1, 2, 3))
-    c1 = _sloppy_corr(U1, g1)
-    delta1 = np.abs(c1[0] - c0[0]) / np.abs(c0[0])
-    assert delta1[:8].max() > 10 * delta[:8].max()
+
+    def delta(g):
+        Ug = np.roll(U, shift=(g[0], g[3], g[2], g[1]), axis=(0, 1, 2, 3))
+        cg = _sloppy_corr(Ug, g)
+        return (np.abs(cg[0] - c0[0]) / np.abs(c0[0]))[:8].max()
+
+    # shift by (2, 1, 0, 1) blocks: Omega -> Omega, Omega* -> Omega*
+    d_even = delta((8, 4, 0, 4))
+    assert d_even < 1e-4, d_even
+    # shift by (1, 1, 0, 1) blocks exchanges Omega and Omega*: M_SAP changes
+    d_odd = delta((4, 4, 0, 4))
+    # shift by one site: the blocks are not mapped onto blocks
+    d_site = delta((1, 0, 0, 0))
+    assert d_odd > 10 * d_even and d_site > 10 * d_even, (d_even, d_odd, d_site)
 
 
 def test_failure_paths(small):
@@ -93,3 +97,5 @@ def test_failure_paths(small):
         lat.solve(to_dev(eta[:1]), 2.0)
     with pytest.raises(QcdError):
         lat.ama_nucleon_2pt([(1, 0, 0, 0)], 1, 1e-3, 1e-10)   # source not block-aligned
+    with pytest.raises(QcdError):
+        lat.ama_nucleon_2pt([(0, 0, 0, 0), (4, 0, 0, 0)], 1, 1e-3, 1e-10)   # odd block shift
