@@ -221,9 +221,15 @@ def kernel_traffic(family_kernel):
         rec = json.load(open(path))[family_kernel]
     except Exception:
         return None
-    src = os.path.join(ROOT, rec["source"])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec if sha == rec.get("source_sha") else None
+    return rec if sources_sha(rec["sources"]) == rec.get("source_sha") else None
+
+
+def sources_sha(paths):
+    """First 16 hex digits of the SHA-256 over the kernel's source files, in order."""
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def run_ours(args):

@@ -534,45 +534,6 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_finish_inner(char* __restrict__ c
   if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = make_double2(v[0], 0.0);
 }
 
-// chi_k *= inv; rho -= ck * chi_k; rho_s = rho in the inner precision; partial |rho|^2
-template <typename X>
-__global__ void __launch_bounds__(GS_TPB) k_gs_finish(char* __restrict__ chik, const double* __restrict__ inv,
-                                                       const double2* __restrict__ ck, char* __restrict__ rho,
-                                                       char* __restrict__ rho_s, int V, double2* __restrict__ part,
-                                                       const int* mask) {
-  __shared__ double sh[32];
-  const int rhs = blockIdx.y;
-  if (mask && !mask[rhs]) return;
-  using R = typename X::R;
-  char* cp = chik + (size_t)rhs * X::bytes * V;
-  char* rp = rho + (size_t)rhs * PD::bytes * V;
-  char* sp = rho_s + (size_t)rhs * X::bytes * V;
-  const R f = (R)inv[rhs];
-  const Cplx<double> c = cmk(ck[rhs].x, ck[rhs].y);
-  double n2 = 0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-      Cplx<R> a, b;
-      X::ld(cp, V, q, s, a, b);
-      a = f * a;
-      b = f * b;
-      X::st(cp, V, q, s, a, b);
-      Cplx<double> x, y;
-      PD::ld(rp, V, q, s, x, y);
-      x = x - c * cmk((double)a.re, (double)a.im);
-      y = y - c * cmk((double)b.re, (double)b.im);
-      PD::st(rp, V, q, s, x, y);
-      X::st(sp, V, q, s, cmk((R)x.re, (R)x.im), cmk((R)y.re, (R)y.im));
-      n2 += x.re * x.re + x.im * x.im + y.re * y.re + y.im * y.im;
-    }
-  }
-  double v[1] = {n2};
-  block_sum_n<1>(v, sh);
-  if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = make_double2(v[0], 0.0);
-}
-
-
 }  // namespace
 
 qcd_status blas_norm2(qcd_ctx* c, const void* x, int prec, int nrhs, double* out_dev, const int* mask) {
@@ -709,27 +670,6 @@ qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, 
     else k_gs_orth_sm<PF, PF, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
   }
   k_sum_parts<<<dim3(2, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 2, G, (double2*)n2c_dev, nrhs,
-                                                        mask);
-  QCD_CUDA_OK(cudaGetLastError());
-  return QCD_OK;
-}
-
-// chi_k *= inv; rho -= ck chi_k; rho_s = (inner precision) rho; rn2[r] = |rho|^2 (as double2 .x)
-qcd_status blas_gs_finish(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev, void* rho,
-                          void* rho_s, int nrhs, double* rn2_dev, const int* mask, int nactive) {
-  const int G = red_grid(c);
-  QCD_TRY(devbuf_ensure(c->red, (size_t)G * nrhs * sizeof(double2)));
-  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
-  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * (3 * vb + 2 * 192), (double)c->g.V * nactive * 96, 2);
-  if (prec == QCD_PREC_F64)
-    k_gs_finish<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
-                                                            (char*)rho, (char*)rho_s, c->g.V, (double2*)c->red.p,
-                                                            mask);
-  else
-    k_gs_finish<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
-                                                            (char*)rho, (char*)rho_s, c->g.V, (double2*)c->red.p,
-                                                            mask);
-  k_sum_parts<<<dim3(1, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 1, G, (double2*)rn2_dev, nrhs,
                                                         mask);
   QCD_CUDA_OK(cudaGetLastError());
   return QCD_OK;

@@ -102,6 +102,28 @@ template <typename R>
 __host__ __device__ inline Cplx<R> cdot(Cplx<R> a, Cplx<R> b) {
   return cmk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
 }
+// Multiply-accumulate in fused steps (two roundings per real part instead of
+// a product, a difference and a sum): acc += a * b, acc += conj(a) * b.
+template <typename R>
+__host__ __device__ inline R rfma(R a, R b, R c);
+template <>
+__host__ __device__ inline float rfma<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__host__ __device__ inline double rfma<double>(double a, double b, double c) { return fma(a, b, c); }
+template <typename R>
+__host__ __device__ inline void cmac(Cplx<R>& acc, Cplx<R> a, Cplx<R> b) {
+  acc.re = rfma(a.re, b.re, acc.re);
+  acc.re = rfma(-a.im, b.im, acc.re);
+  acc.im = rfma(a.re, b.im, acc.im);
+  acc.im = rfma(a.im, b.re, acc.im);
+}
+template <typename R>
+__host__ __device__ inline void cmac_conj(Cplx<R>& acc, Cplx<R> a, Cplx<R> b) {
+  acc.re = rfma(a.re, b.re, acc.re);
+  acc.re = rfma(a.im, b.im, acc.re);
+  acc.im = rfma(a.re, b.im, acc.im);
+  acc.im = rfma(-a.im, b.re, acc.im);
+}
 // i * a, -i * a
 template <typename R>
 __host__ __device__ inline Cplx<R> mul_i(Cplx<R> a) { return cmk(-a.im, a.re); }
@@ -177,8 +199,12 @@ __host__ __device__ inline HalfSpinor<R> su3_mul(const SU3<R>& U, const HalfSpin
 #pragma unroll
   for (int s = 0; s < 2; s++)
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-      o.c[3 * s + a] = U.m[a][0] * h.c[3 * s] + U.m[a][1] * h.c[3 * s + 1] + U.m[a][2] * h.c[3 * s + 2];
+    for (int a = 0; a < 3; a++) {
+      Cplx<R> acc = U.m[a][0] * h.c[3 * s];
+      cmac(acc, U.m[a][1], h.c[3 * s + 1]);
+      cmac(acc, U.m[a][2], h.c[3 * s + 2]);
+      o.c[3 * s + a] = acc;
+    }
   return o;
 }
 template <typename R>
@@ -187,8 +213,12 @@ __host__ __device__ inline HalfSpinor<R> su3_dag_mul(const SU3<R>& U, const Half
 #pragma unroll
   for (int s = 0; s < 2; s++)
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-      o.c[3 * s + a] = cdot(U.m[0][a], h.c[3 * s]) + cdot(U.m[1][a], h.c[3 * s + 1]) + cdot(U.m[2][a], h.c[3 * s + 2]);
+    for (int a = 0; a < 3; a++) {
+      Cplx<R> acc = cdot(U.m[0][a], h.c[3 * s]);
+      cmac_conj(acc, U.m[1][a], h.c[3 * s + 1]);
+      cmac_conj(acc, U.m[2][a], h.c[3 * s + 2]);
+      o.c[3 * s + a] = acc;
+    }
   return o;
 }
 
@@ -280,8 +310,8 @@ __host__ __device__ inline void clover_block_apply(const R* cl, int k0, const Cp
     for (int j = 0; j < i; j++) {
       Cplx<R> h = cmk(cl[k], cl[k + 1]);
       k += 2;
-      out[i] = out[i] + h * v[j];
-      out[j] = out[j] + cdot(h, v[i]);
+      cmac(out[i], h, v[j]);
+      cmac_conj(out[j], h, v[i]);
     }
   }
 }
@@ -398,8 +428,6 @@ qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, 
 // chi_k *= inv; rho -= ck chi_k, rho in the inner precision prec
 qcd_status blas_gs_finish_inner(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev,
                                 void* rho, int nrhs, double* rn2_dev, const int* mask, int nactive);
-qcd_status blas_gs_finish(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev, void* rho,
-                          void* rho_s, int nrhs, double* rn2_dev, const int* mask, int nactive);
 // out = x - y
 qcd_status blas_xmy(qcd_ctx* c, const void* x, const void* y, void* out, int prec, int nrhs, const int* mask);
 

@@ -106,7 +106,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(const char* __restrict
   Cplx<R>* r_s = (Cplx<R>*)smem_raw;
   __shared__ R red[3][32];
 
-  const int rhs = blockIdx.y;
+  // the RHS index runs fastest over the grid: the CTAs of one block (all RHS)
+  // are resident together and share its links and clover term through L2
+  const int rhs = blockIdx.x % nrhs;
+  const int blk = blockIdx.x / nrhs;
   if (mask && !mask[rhs]) return;
   const size_t off = (size_t)rhs * F::spinor_bytes * g.V;
   rho_src += off;
@@ -114,10 +117,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(const char* __restrict
   psi += off;
   delta += off;
 
-  // which block: the blockIdx.x-th block of this colour
+  // which block: the blk-th block of this colour
   const int nbx2 = sg.nb[1] >> 1;
-  int q = blockIdx.x / nbx2;
-  const int j = blockIdx.x - q * nbx2;
+  int q = blk / nbx2;
+  const int j = blk - q * nbx2;
   const int by = q % sg.nb[2];
   q /= sg.nb[2];
   const int bz = q % sg.nb[3];
@@ -163,13 +166,15 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(const char* __restrict
     block_hop<F, 2>(p, r_s, sg, gauge, g, s, l, lc, -kappa);
     block_hop<F, 3>(p, r_s, sg, gauge, g, s, l, lc, -kappa);
     // alpha = (p, r) / (p, p) over the block
-    R pr_re = 0, pr_im = 0, pp = 0;
+    Cplx<R> pr = cmk((R)0, (R)0);
+    R pp = 0;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      pr_re += p.c[k].re * r.c[k].re + p.c[k].im * r.c[k].im;
-      pr_im += p.c[k].re * r.c[k].im - p.c[k].im * r.c[k].re;
-      pp += p.c[k].re * p.c[k].re + p.c[k].im * p.c[k].im;
+      cmac_conj(pr, p.c[k], r.c[k]);
+      pp = rfma(p.c[k].re, p.c[k].re, pp);
+      pp = rfma(p.c[k].im, p.c[k].im, pp);
     }
+    R pr_re = pr.re, pr_im = pr.im;
     pr_re = warp_sum(pr_re);
     pr_im = warp_sum(pr_im);
     pp = warp_sum(pp);
@@ -186,10 +191,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_sweep(const char* __restrict
       n2 += red[2][w];
     }
     Cplx<R> alpha = n2 > (R)0 ? cmk(a_re / n2, a_im / n2) : cmk((R)0, (R)0);
+    const Cplx<R> malpha = -alpha;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      x.c[k] = x.c[k] + alpha * r.c[k];
-      r.c[k] = r.c[k] - alpha * p.c[k];
+      cmac(x.c[k], alpha, r.c[k]);
+      cmac(r.c[k], malpha, p.c[k]);
     }
     __syncthreads();
     smem_store(r_s, sg.vb, l, r);
@@ -354,7 +360,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
   W* cl_s = (W*)(lk_s + (size_t)36 * vb);                                 // [18][vb]
   __shared__ float red[3][32];
 
-  const int rhs = blockIdx.y;
+  const int rhs = blockIdx.x % nrhs;   // RHS fastest, as in k_sap_sweep
+  const int blk = blockIdx.x / nrhs;
   if (mask && !mask[rhs]) return;
   const size_t off = (size_t)rhs * FieldsF::spinor_bytes * g.V;
   rho_src += off;
@@ -363,8 +370,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
   delta += off;
 
   const int nbx2 = sg.nb[1] >> 1;
-  int q = blockIdx.x / nbx2;
-  const int j = blockIdx.x - q * nbx2;
+  int q = blk / nbx2;
+  const int j = blk - q * nbx2;
   const int by = q % sg.nb[2];
   q /= sg.nb[2];
   const int bz = q % sg.nb[3];
@@ -417,13 +424,15 @@ __global__ void __launch_bounds__(MAXT, MINB)
     smem_block_hop<S, BF, 1>(p, r_s, lk_s, sg, l, lc, -kappa);
     smem_block_hop<S, BF, 2>(p, r_s, lk_s, sg, l, lc, -kappa);
     smem_block_hop<S, BF, 3>(p, r_s, lk_s, sg, l, lc, -kappa);
-    float pr_re = 0, pr_im = 0, pp = 0;
+    Cplx<float> pr = cmk(0.f, 0.f);
+    float pp = 0;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      pr_re += p.c[k].re * r.c[k].re + p.c[k].im * r.c[k].im;
-      pr_im += p.c[k].re * r.c[k].im - p.c[k].im * r.c[k].re;
-      pp += p.c[k].re * p.c[k].re + p.c[k].im * p.c[k].im;
+      cmac_conj(pr, p.c[k], r.c[k]);
+      pp = fmaf(p.c[k].re, p.c[k].re, pp);
+      pp = fmaf(p.c[k].im, p.c[k].im, pp);
     }
+    float pr_re = pr.re, pr_im = pr.im;
     pr_re = warp_sum(pr_re);
     pr_im = warp_sum(pr_im);
     pp = warp_sum(pp);
@@ -440,10 +449,11 @@ __global__ void __launch_bounds__(MAXT, MINB)
       n2 += red[2][w];
     }
     Cplx<float> alpha = n2 > 0.f ? cmk(a_re / n2, a_im / n2) : cmk(0.f, 0.f);
+    const Cplx<float> malpha = -alpha;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      x.c[k] = x.c[k] + alpha * r.c[k];
-      r.c[k] = r.c[k] - alpha * p.c[k];
+      cmac(x.c[k], alpha, r.c[k]);
+      cmac(r.c[k], malpha, p.c[k]);
     }
     __syncthreads();
     rs_store<BF>(r_s, vb, l, r);
@@ -485,7 +495,7 @@ qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, 
               : sg.vb <= 512 ? k_sap_sweep<F, 512, 1>
                              : k_sap_sweep<F, 1024, 1>;
   QCD_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(nblocks / 2, nrhs);
+  const dim3 grid((unsigned)(nblocks / 2) * (unsigned)nrhs);
   // Algorithmic cost of one half-cycle (the minimum each launch must move):
   // per active site and RHS, rho read and written, psi read and written (only
   // written in the first cycle), delta written, and the other colour's delta
@@ -502,7 +512,8 @@ qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, 
   const double f_face = 1.0 - (inner > 0 ? inner : 0.0);
   const double sb = (double)F::spinor_bytes, lb = (double)F::link_bytes, cb = (double)F::clover_bytes;
   const double half = c->g.V / 2.0;
-  const double flops_site = P.nmr * (1320.0 * (1.0 - face / 8.0) + 504.0 + 192.0) + 165.0 * face;
+  const double flops_gather = 165.0 * face;
+  const double flops_site = P.nmr * (1320.0 * (1.0 - face / 8.0) + 504.0 + 192.0) + flops_gather;
   const int fam = sizeof(typename F::R) == 8 ? FAM_SAP_D : FAM_SAP_F;
   // FP32 with blocks of at most 256 sites: the shared-memory-resident kernel
   const bool resident = sizeof(typename F::R) == 4 && sg.vb <= 256;
@@ -519,16 +530,18 @@ qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, 
     for (int cy = 0; cy < P.ncy; cy++)
       for (int col = 0; col < 2; col++) {
         const int first = cy == 0 && !accumulate;
-        const double bytes_rhs = sb * (2 + (first ? 1 : 2) + 1 + f_face);
-        ProfScope ps(c, fam, half * (nactive * bytes_rhs + 4 * lb + cb), half * nactive * flops_site);
+        const int gather = !(cy == 0 && col == 0);   // no boundary term before the first half-cycle
+        const double bytes_rhs = sb * (2 + (first ? 1 : 2) + 1 + (gather ? f_face : 0.0));
+        ProfScope ps(c, fam, half * (nactive * bytes_rhs + 4 * lb + cb),
+                     half * nactive * (flops_site - (gather ? 0.0 : flops_gather)));
         const char* rin = cy == 0 ? rho_src : rho;   // the first cycle reads the caller's residual
         if (resident)
           kres<<<grid, sg.vb, smem_res, c->stream>>>(rin, rho, psi, delta, (const float4*)gauge, (const float4*)clover,
-                                                     c->g, sg, col, !(cy == 0 && col == 0), first, (float)c->kappa,
+                                                     c->g, sg, col, gather, first, (float)c->kappa,
                                                      P.nmr, nrhs, mask);
         else
           kern<<<grid, sg.vb, smem, c->stream>>>(rin, rho, psi, delta, gauge, clover, c->g, sg, col,
-                                                 !(cy == 0 && col == 0), first, (typename F::R)c->kappa, P.nmr, nrhs,
+                                                 gather, first, (typename F::R)c->kappa, P.nmr, nrhs,
                                                  mask);
         QCD_CUDA_OK(cudaGetLastError());
       }
@@ -572,11 +585,13 @@ qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, 
     c->sap_graphs.push_back(key);
   }
   double bytes = 0, flops = 0;
-  for (int cy = 0; cy < P.ncy; cy++) {
-    const int first = cy == 0 && !accumulate;
-    bytes += 2 * half * (nactive * sb * (2 + (first ? 1 : 2) + 1 + f_face) + 4 * lb + cb);
-    flops += 2 * half * nactive * flops_site;
-  }
+  for (int cy = 0; cy < P.ncy; cy++)
+    for (int col = 0; col < 2; col++) {
+      const int first = cy == 0 && !accumulate;
+      const int gather = !(cy == 0 && col == 0);
+      bytes += half * (nactive * sb * (2 + (first ? 1 : 2) + 1 + (gather ? f_face : 0.0)) + 4 * lb + cb);
+      flops += half * nactive * (flops_site - (gather ? 0.0 : flops_gather));
+    }
   ProfScope ps(c, fam, bytes, flops, 2 * P.ncy);
   QCD_CUDA_OK(cudaGraphLaunch(exec, c->stream));
   return QCD_OK;
