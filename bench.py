@@ -219,9 +219,10 @@ def kernel_traffic(family_kernel):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         rec = json.load(open(path))[family_kernel]
-    except Exception:
+        current = sources_sha(rec["sources"]) == rec["source_sha"]
+    except (OSError, ValueError, KeyError, TypeError):
         return None
-    return rec if sources_sha(rec["sources"]) == rec.get("source_sha") else None
+    return rec if current else None
 
 
 def sources_sha(paths):
@@ -230,6 +231,33 @@ def sources_sha(paths):
     for p in paths:
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
+
+
+def roofline(prof, ms, clk, pk):
+    """Roofline record of the dominant kernel family of the timed region, from the
+    library's per-family records (bytes, flops, launches, ms), the step time ms,
+    the sampled clocks and the measured peaks."""
+    fam = max(prof, key=lambda k: prof[k]["ms"])
+    f = prof[fam]
+    mhz = clk["sm_mhz"] if clk and clk.get("sm_mhz") else pk.get("sm_max_mhz", 2070)
+    ridge = FP32_ALU_TFLOPS_PER_GHZ * (mhz / 1000.0) * 1e12 / (pk["hbm_gbs"] * 1e9)
+    ai = f["flops"] / max(f["bytes"], 1)
+    per_launch_bytes = f["bytes"] / max(f["launches"], 1)
+    tr = kernel_traffic(fam)
+    if ai < ridge:
+        achieved = f["bytes"] / f["ms"] / 1e6
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 3)}
+    else:
+        achieved = f["flops"] / f["ms"] / 1e9
+        alu_peak = FP32_ALU_TFLOPS_PER_GHZ * pk.get("sm_max_mhz", 2070) / 1000.0
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / alu_peak, 3)}
+    roof.update({"kernel": fam, "launches": f["launches"], "share_of_step": round(f["ms"] / ms, 3),
+                 "algorithmic_bytes_per_launch": int(per_launch_bytes), "flops_per_byte": round(ai, 2),
+                 "traffic": (int(tr["bytes_per_alg_byte"] * per_launch_bytes) if tr else None),
+                 "peak_source": "MEASURED_PEAKS.json" if not pk.get("_fallback") else "fallback"})
+    return roof
 
 
 def run_ours(args):
@@ -328,27 +356,7 @@ def run_ours(args):
         lat.set_params(precision="f32", rhs_tile=0, max_outer=WORKLOAD["max_outer"],
                        restart_drop=WORKLOAD["restart_drop"])
 
-    # roofline of the dominant kernel family inside the timed region
-    fam = max(prof, key=lambda k: prof[k]["ms"])
-    f = prof[fam]
-    ridge = FP32_ALU_TFLOPS_PER_GHZ * (clk["sm_mhz"] / 1000.0 if clk else pk.get("sm_max_mhz", 2070) / 1000.0) \
-        * 1e12 / (pk["hbm_gbs"] * 1e9)
-    ai = f["flops"] / max(f["bytes"], 1)
-    per_launch_bytes = f["bytes"] / f["launches"]
-    tr = kernel_traffic(fam)
-    if ai < ridge:
-        achieved = f["bytes"] / f["ms"] / 1e6
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 3)}
-    else:
-        achieved = f["flops"] / f["ms"] / 1e9
-        alu_peak = FP32_ALU_TFLOPS_PER_GHZ * pk.get("sm_max_mhz", 2070) / 1000.0
-        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / alu_peak, 3)}
-    roof.update({"kernel": fam, "launches": f["launches"], "share_of_step": round(f["ms"] / ms, 3),
-                 "algorithmic_bytes_per_launch": int(per_launch_bytes), "flops_per_byte": round(ai, 2),
-                 "traffic": (int(tr["bytes_per_alg_byte"] * per_launch_bytes) if tr else None),
-                 "peak_source": "MEASURED_PEAKS.json" if not pk.get("_fallback") else "fallback"})
+    roof = roofline(prof, ms, clk, peaks())
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
