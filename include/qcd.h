@@ -93,6 +93,13 @@ typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
  *               GCR is unaffected in what it converges to); 2 = in addition the
  *               block residual read by neighbouring sites is held as bf16;
  *               0 = FP32 copies.
+ *   basis_half  QCD_PREC_F32 only: 1 = the GCR images chi_k = D phi_k are
+ *               stored as FP16 with one FP32 scale per site (52 bytes per site
+ *               instead of 96; arithmetic stays FP32).  The recursive residual
+ *               then carries the FP16 rounding (about 3e-4 relative), so it is
+ *               meant for sloppy tolerances; convergence is still decided by
+ *               the FP64 true residual.  qcd_ama_nucleon_2pt applies it to the
+ *               sloppy solves only.  0 = FP32 storage.  Ignored for QCD_PREC_F64.
  */
 typedef struct {
   int block[4];
@@ -108,6 +115,7 @@ typedef struct {
   int dfl_little_iters;
   int dfl_gen_iters;
   int graphs;
+  int basis_half;
 } qcd_solver_params;
 
 /* Per right-hand-side outcome of a solve. */
@@ -138,7 +146,7 @@ qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int U_on_device, double
 
 /* Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
  * restart_drop 1e-5, precision F32, rhs_tile 0, sap_half 0, dfl 1,
- * dfl_little_iters 16, dfl_gen_iters 0, graphs 1. */
+ * dfl_little_iters 16, dfl_gen_iters 0, graphs 1, basis_half 0. */
 void qcd_default_params(qcd_solver_params* p);
 qcd_status qcd_set_params(qcd_ctx* ctx, const qcd_solver_params* p);
 

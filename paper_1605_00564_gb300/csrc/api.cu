@@ -122,6 +122,7 @@ qcd_status validate_params(const qcd_ctx* c, const qcd_solver_params* p) {
   ARG_CHECK(p->dfl_little_iters >= 1 && p->dfl_little_iters <= 64, "dfl_little_iters must be in [1, 64]");
   ARG_CHECK(p->dfl_gen_iters >= 0 && p->dfl_gen_iters <= 64, "dfl_gen_iters must be in [0, 64]");
   ARG_CHECK(p->graphs == 0 || p->graphs == 1, "graphs must be 0 or 1");
+  ARG_CHECK(p->basis_half == 0 || p->basis_half == 1, "basis_half must be 0 or 1");
   return QCD_OK;
 }
 
@@ -165,6 +166,7 @@ void qcd_default_params(qcd_solver_params* p) {
   p->dfl_little_iters = 16;
   p->dfl_gen_iters = 0;
   p->graphs = 1;
+  p->basis_half = 0;
 }
 
 qcd_status qcd_create(qcd_ctx** out, const int dims[4], void* cuda_stream) {
@@ -446,7 +448,11 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* c, const int* src, int n_src, int n_exac
       ProfScope ps(c, FAM_LAYOUT, 0.0, 0.0);
       k_point_sources<<<(n + 63) / 64, 64, 0, c->stream>>>((double2*)c->wsD[0].p, d_sites, c->g.V, n);
     }
+    // an FP16 Krylov basis (basis_half) serves the sloppy tiles only
+    const int basis_half = c->params.basis_half;
+    if (j0 >= n_src) c->params.basis_half = 0;
     rc = solver_run(c, n, tols.data(), st.data() + (size_t)12 * j0);
+    c->params.basis_half = basis_half;
     if (rc != QCD_OK) break;
     if (j0 < n_src)
       for (int k = 0; k < nj; k++)

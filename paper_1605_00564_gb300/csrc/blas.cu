@@ -6,6 +6,8 @@
 // A spinor of either precision is viewed as 6 V "pairs" of complex numbers:
 // pair (k, s) holds components 2k and 2k+1 of site s.  FP32 stores a pair as
 // one float4 at k*V + s; FP64 as two double2 at 2k*V + s and (2k+1)*V + s.
+#include <type_traits>
+
 #include "qcd_internal.cuh"
 
 namespace {
@@ -39,6 +41,50 @@ struct PF {  // FP32 pair access
     ((float4*)b)[(size_t)k * V + s] = make_float4(a.re, a.im, c.re, c.im);
   }
 };
+
+// Whole-site access (all 12 components), the form the site-major kernels use.
+template <typename X>
+__device__ inline void ld_site(const char* b, int V, int s, Cplx<typename X::R> (&a)[12]) {
+#pragma unroll
+  for (int q = 0; q < 6; q++) X::ld(b, V, q, s, a[2 * q], a[2 * q + 1]);
+}
+template <typename X>
+__device__ inline void st_site(char* b, int V, int s, const Cplx<typename X::R> (&a)[12]) {
+#pragma unroll
+  for (int q = 0; q < 6; q++) X::st(b, V, q, s, a[2 * q], a[2 * q + 1]);
+}
+struct PH {  // FP16 + per-site scale (FieldsH layout); whole-site access only
+  using R = float;
+  static constexpr size_t bytes = FieldsH::spinor_bytes;
+};
+template <>
+__device__ inline void ld_site<PH>(const char* b, int V, int s, Cplx<float> (&a)[12]) {
+  const Spinor<float> v = FieldsH::load_spinor(b, V, s);
+#pragma unroll
+  for (int q = 0; q < 12; q++) a[q] = v.c[q];
+}
+template <>
+__device__ inline void st_site<PH>(char* b, int V, int s, const Cplx<float> (&a)[12]) {
+  Spinor<float> v;
+#pragma unroll
+  for (int q = 0; q < 12; q++) v.c[q] = a[q];
+  FieldsH::store_spinor(b, V, s, v);
+}
+// a <- the values a later load of st_site(a) returns (identity except for PH)
+template <typename X>
+__device__ inline void round_site(Cplx<typename X::R> (&)[12]) {}
+template <>
+__device__ inline void round_site<PH>(Cplx<float> (&a)[12]) {
+  Spinor<float> v;
+#pragma unroll
+  for (int q = 0; q < 12; q++) v.c[q] = a[q];
+  uint2 w[6];
+  float sc;
+  FieldsH::encode(v, w, sc);
+  v = FieldsH::decode(w, sc);
+#pragma unroll
+  for (int q = 0; q < 12; q++) a[q] = v.c[q];
+}
 
 // arithmetic type of a mixed product: FP32 only when both sides are FP32
 template <typename X, typename Y>
@@ -324,18 +370,17 @@ __global__ void __launch_bounds__(GS_TPB) k_multi_dot_acc(const char* __restrict
   for (int j = 0; j < KMAX; j++) ar[j] = ai[j] = (R)0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
     Cplx<R> ck[12];
-#pragma unroll
-    for (int q = 0; q < 6; q++) X::ld(chi + k * jstride + roff, V, q, s, ck[2 * q], ck[2 * q + 1]);
+    ld_site<X>(chi + k * jstride + roff, V, s, ck);
 #pragma unroll
     for (int j = 0; j < KMAX; j++) {
       if (j < k) {
+        Cplx<R> u[12];
+        ld_site<X>(chi + j * jstride + roff, V, s, u);
+        Cplx<R> d = cmk((R)0, (R)0);
 #pragma unroll
-        for (int q = 0; q < 6; q++) {
-          Cplx<R> a, b;
-          X::ld(chi + j * jstride + roff, V, q, s, a, b);
-          ar[j] += a.re * ck[2 * q].re + a.im * ck[2 * q].im + b.re * ck[2 * q + 1].re + b.im * ck[2 * q + 1].im;
-          ai[j] += a.re * ck[2 * q].im - a.im * ck[2 * q].re + b.re * ck[2 * q + 1].im - b.im * ck[2 * q + 1].re;
-        }
+        for (int q = 0; q < 12; q++) cmac_conj(d, u[q], ck[q]);
+        ar[j] += d.re;
+        ai[j] += d.im;
       }
     }
   }
@@ -429,29 +474,26 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, s
   double n2 = 0, cr = 0, ci = 0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
     Cplx<R> a[12];
-#pragma unroll
-    for (int q = 0; q < 6; q++) X::ld(ckp, V, q, s, a[2 * q], a[2 * q + 1]);
+    ld_site<X>(ckp, V, s, a);
 #pragma unroll
     for (int j = 0; j < KMAX; j++) {
       if (j < k) {
         Cplx<R> u[12];
+        ld_site<X>(chi + j * jstride + roff, V, s, u);
+        const Cplx<R> mw = cmk((R)-w_s[j].x, (R)-w_s[j].y);
 #pragma unroll
-        for (int q = 0; q < 6; q++) X::ld(chi + j * jstride + roff, V, q, s, u[2 * q], u[2 * q + 1]);
-        const Cplx<R> w = cmk((R)w_s[j].x, (R)w_s[j].y);
-#pragma unroll
-        for (int q = 0; q < 12; q++) a[q] = a[q] - w * u[q];
+        for (int q = 0; q < 12; q++) cmac(a[q], mw, u[q]);
       }
     }
+    st_site<X>(ckp, V, s, a);
+    round_site<X>(a);   // the norm and the overlap with rho of chi_k as stored
+    Cplx<typename RH::R> x[12];
+    ld_site<RH>(rp, V, s, x);
 #pragma unroll
-    for (int q = 0; q < 6; q++) X::st(ckp, V, q, s, a[2 * q], a[2 * q + 1]);
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-      Cplx<typename RH::R> x, y;
-      RH::ld(rp, V, q, s, x, y);
-      const Cplx<R> p0 = a[2 * q], p1 = a[2 * q + 1];
-      n2 += (double)(p0.re * p0.re + p0.im * p0.im + p1.re * p1.re + p1.im * p1.im);
-      cr += (double)p0.re * x.re + (double)p0.im * x.im + (double)p1.re * y.re + (double)p1.im * y.im;
-      ci += (double)p0.re * x.im - (double)p0.im * x.re + (double)p1.re * y.im - (double)p1.im * y.re;
+    for (int q = 0; q < 12; q++) {
+      n2 += (double)(a[q].re * a[q].re + a[q].im * a[q].im);
+      cr += (double)a[q].re * x[q].re + (double)a[q].im * x[q].im;
+      ci += (double)a[q].re * x[q].im - (double)a[q].im * x[q].re;
     }
   }
   double v[3] = {n2, cr, ci};
@@ -498,35 +540,47 @@ __global__ void __launch_bounds__(GS_TPB) k_caxpy_sm(char* __restrict__ y, const
   }
 }
 
-// chi_k *= inv; rho -= ck * chi_k with rho in the inner precision X; partial |rho|^2
-template <typename X>
+// chi_k *= inv; rho -= ck * chi_k; chi_k stored as XC, rho in the inner
+// precision XR (the same real type); partial |rho|^2
+template <typename XC, typename XR>
 __global__ void __launch_bounds__(GS_TPB) k_gs_finish_inner(char* __restrict__ chik, const double* __restrict__ inv,
                                                              const double2* __restrict__ ck, char* __restrict__ rho,
                                                              int V, double2* __restrict__ part, const int* mask) {
   __shared__ double sh[32];
   const int rhs = blockIdx.y;
   if (mask && !mask[rhs]) return;
-  using R = typename X::R;
-  char* cp = chik + (size_t)rhs * X::bytes * V;
-  char* rp = rho + (size_t)rhs * X::bytes * V;
+  using R = typename XR::R;
+  char* cp = chik + (size_t)rhs * XC::bytes * V;
+  char* rp = rho + (size_t)rhs * XR::bytes * V;
   const R f = (R)inv[rhs];
-  const Cplx<R> c = cmk((R)ck[rhs].x, (R)ck[rhs].y);
+  const Cplx<R> mc = cmk((R)-ck[rhs].x, (R)-ck[rhs].y);
   double n2 = 0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+    Cplx<R> a[12], x[12];
+    ld_site<XR>(rp, V, s, x);
+    if constexpr (std::is_same<XC, PH>::value) {
+      // FP16 words unchanged; only the site's scale factor takes the normalisation
+      uint2 w[6];
+      float sc;
+      FieldsH::load_words(cp, V, s, w, sc);
+      sc *= (float)f;
+      const Spinor<float> v = FieldsH::decode(w, sc);
+#pragma unroll
+      for (int q = 0; q < 12; q++) a[q] = cmk((R)v.c[q].re, (R)v.c[q].im);
+      ((float*)FieldsH::scale_ptr(cp, V))[s] = sc;
+    } else {
+      ld_site<XC>(cp, V, s, a);
+#pragma unroll
+      for (int q = 0; q < 12; q++) a[q] = f * a[q];
+      st_site<XC>(cp, V, s, a);
+    }
     R acc = 0;
 #pragma unroll
-    for (int q = 0; q < 6; q++) {
-      Cplx<R> a, b, x, y;
-      X::ld(cp, V, q, s, a, b);
-      X::ld(rp, V, q, s, x, y);
-      a = f * a;
-      b = f * b;
-      x = x - c * a;
-      y = y - c * b;
-      X::st(cp, V, q, s, a, b);
-      X::st(rp, V, q, s, x, y);
-      acc += x.re * x.re + x.im * x.im + y.re * y.re + y.im * y.im;
+    for (int q = 0; q < 12; q++) {
+      cmac(x[q], mc, a[q]);
+      acc += x[q].re * x[q].re + x[q].im * x[q].im;
     }
+    st_site<XR>(rp, V, s, x);
     n2 += (double)acc;
   }
   double v[1] = {n2};
@@ -625,12 +679,16 @@ qcd_status blas_gs_dots(qcd_ctx* c, const void* chi, int prec, size_t jstride, i
   if (k <= 0) return QCD_OK;
   const int G = red_grid(c);
   QCD_TRY(devbuf_ensure(c->red, (size_t)G * k * nrhs * sizeof(double2)));
-  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
+  const double vb = prec == QCD_PREC_F64 ? 192 : prec == QCD_PREC_H16 ? (double)PH::bytes : 96;
   ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * (k + 1) * vb, (double)c->g.V * nactive * k * 48, 2);
   const dim3 grid(G, nrhs);
   const char* cp = (const char*)chi;
   double2* pp = (double2*)c->red.p;
-  if (prec == QCD_PREC_F64) {
+  if (prec == QCD_PREC_H16) {
+    if (k <= 8) k_multi_dot_acc<PH, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+    else if (k <= 16) k_multi_dot_acc<PH, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+    else k_multi_dot_acc<PH, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
+  } else if (prec == QCD_PREC_F64) {
     if (k <= 8) k_multi_dot_acc<PD, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
     else if (k <= 16) k_multi_dot_acc<PD, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
     else k_multi_dot_acc<PD, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, c->g.V, pp, mask);
@@ -650,7 +708,7 @@ qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, 
                         const void* rho, int prho, int nrhs, double* n2c_dev, const int* mask, int nactive) {
   const int G = red_grid(c);
   QCD_TRY(devbuf_ensure(c->red, (size_t)G * 2 * nrhs * sizeof(double2)));
-  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
+  const double vb = prec == QCD_PREC_F64 ? 192 : prec == QCD_PREC_H16 ? (double)PH::bytes : 96;
   ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * ((k + 2) * vb + (prho == QCD_PREC_F64 ? 192 : 96)),
                (double)c->g.V * nactive * (k + 2) * 48, 2);
   const dim3 grid(G, nrhs);
@@ -658,7 +716,15 @@ qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, 
   const double2* dp = (const double2*)dots_dev;
   const char* rp = (const char*)rho;
   double2* pp = (double2*)c->red.p;
-  if (prec == QCD_PREC_F64)
+  if (prec == QCD_PREC_H16) {
+    if (prho != QCD_PREC_F32) {
+      qcd_set_error("gs_orth: an FP16 basis needs an FP32 residual");
+      return QCD_ERR_ARG;
+    }
+    if (k <= 8) k_gs_orth_sm<PH, PF, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+    else if (k <= 16) k_gs_orth_sm<PH, PF, 16><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+    else k_gs_orth_sm<PH, PF, 32><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
+  } else if (prec == QCD_PREC_F64)
     k_gs_orth<PD><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
   else if (prho == QCD_PREC_F64) {
     if (k <= 8) k_gs_orth_sm<PF, PD, 8><<<grid, GS_TPB, 0, c->stream>>>(cp, jstride, k, dp, rp, c->g.V, nrhs, pp, mask);
@@ -676,18 +742,31 @@ qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, 
 }
 
 // chi_k *= inv; rho -= ck chi_k with rho in the inner precision; rn2[r] = |rho|^2 (double2 .x)
-qcd_status blas_gs_finish_inner(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev,
-                                void* rho, int nrhs, double* rn2_dev, const int* mask, int nactive) {
+qcd_status blas_gs_finish_inner(qcd_ctx* c, void* chik, int pchi, const double* inv_dev, const double* ck_dev,
+                                void* rho, int prho, int nrhs, double* rn2_dev, const int* mask, int nactive) {
+  const bool h16 = pchi == QCD_PREC_H16 && prho == QCD_PREC_F32;
+  const bool f64 = pchi == QCD_PREC_F64 && prho == QCD_PREC_F64;
+  const bool f32 = pchi == QCD_PREC_F32 && prho == QCD_PREC_F32;
+  if (!h16 && !f64 && !f32) {
+    qcd_set_error("gs_finish: unsupported precision pair");
+    return QCD_ERR_ARG;
+  }
   const int G = red_grid(c);
   QCD_TRY(devbuf_ensure(c->red, (size_t)G * nrhs * sizeof(double2)));
-  const double vb = prec == QCD_PREC_F64 ? 192 : 96;
-  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * 4 * vb, (double)c->g.V * nactive * 96, 2);
-  if (prec == QCD_PREC_F64)
-    k_gs_finish_inner<PD><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
-                                                                  (char*)rho, c->g.V, (double2*)c->red.p, mask);
+  const dim3 grid(G, nrhs);
+  char* cp = (char*)chik;
+  const double2* kp = (const double2*)ck_dev;
+  char* rp = (char*)rho;
+  double2* pp = (double2*)c->red.p;
+  // FP16 basis: chi_k read (words + scale) and only its scale written; rho read and written
+  const double bytes = h16 ? PH::bytes + 4.0 + 2 * 96 : 4.0 * (f64 ? 192 : 96);
+  ProfScope ps(c, FAM_BLAS, (double)c->g.V * nactive * bytes, (double)c->g.V * nactive * 96, 2);
+  if (h16)
+    k_gs_finish_inner<PH, PF><<<grid, GS_TPB, 0, c->stream>>>(cp, inv_dev, kp, rp, c->g.V, pp, mask);
+  else if (f64)
+    k_gs_finish_inner<PD, PD><<<grid, GS_TPB, 0, c->stream>>>(cp, inv_dev, kp, rp, c->g.V, pp, mask);
   else
-    k_gs_finish_inner<PF><<<dim3(G, nrhs), GS_TPB, 0, c->stream>>>((char*)chik, inv_dev, (const double2*)ck_dev,
-                                                                  (char*)rho, c->g.V, (double2*)c->red.p, mask);
+    k_gs_finish_inner<PF, PF><<<grid, GS_TPB, 0, c->stream>>>(cp, inv_dev, kp, rp, c->g.V, pp, mask);
   k_sum_parts<<<dim3(1, nrhs), RED_TPB, 0, c->stream>>>((const double2*)c->red.p, 1, G, (double2*)rn2_dev, nrhs,
                                                         mask);
   QCD_CUDA_OK(cudaGetLastError());

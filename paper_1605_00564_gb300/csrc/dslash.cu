@@ -37,7 +37,8 @@ __device__ inline void hop_dir(Spinor<typename F::R>& acc, const void* in, const
   }
 }
 
-template <typename F, int DAGGER>
+// O: storage of the output (F itself, or FieldsH for FP16 + per-site scale)
+template <typename F, typename O, int DAGGER>
 __global__ void __launch_bounds__(DSLASH_TPB) k_dslash(const char* __restrict__ in, char* __restrict__ out,
                                                        const void* __restrict__ gauge, const void* __restrict__ clover,
                                                        Geom g, typename F::R kappa, int nrhs, const int* mask) {
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(DSLASH_TPB) k_dslash(const char* __restrict__ 
   if (s >= g.V) return;
   if (mask && !mask[rhs]) return;
   const size_t off = (size_t)rhs * F::spinor_bytes * g.V;
+  const size_t off_out = (size_t)rhs * O::spinor_bytes * g.V;
   const void* src = in + off;
   int c[4];
   site_coords(g, s, c);
@@ -55,20 +57,20 @@ __global__ void __launch_bounds__(DSLASH_TPB) k_dslash(const char* __restrict__ 
   hop_dir<F, 1, DAGGER>(o, src, gauge, g, s, c, -kappa);
   hop_dir<F, 2, DAGGER>(o, src, gauge, g, s, c, -kappa);
   hop_dir<F, 3, DAGGER>(o, src, gauge, g, s, c, -kappa);
-  F::store_spinor(out + off, g.V, s, o);
+  O::store_spinor(out + off_out, g.V, s, o);
 }
 
-template <typename F>
+template <typename F, typename O = F>
 qcd_status launch(qcd_ctx* c, const void* in, void* out, const void* gauge, const void* clover, int nrhs, int dagger,
                   const int* mask) {
   int nb = (c->g.V + DSLASH_TPB - 1) / DSLASH_TPB;
   dim3 grid((unsigned)nb * nrhs);
   if (dagger)
-    k_dslash<F, 1><<<grid, DSLASH_TPB, 0, c->stream>>>((const char*)in, (char*)out, gauge, clover, c->g,
-                                                       (typename F::R)c->kappa, nrhs, mask);
+    k_dslash<F, O, 1><<<grid, DSLASH_TPB, 0, c->stream>>>((const char*)in, (char*)out, gauge, clover, c->g,
+                                                          (typename F::R)c->kappa, nrhs, mask);
   else
-    k_dslash<F, 0><<<grid, DSLASH_TPB, 0, c->stream>>>((const char*)in, (char*)out, gauge, clover, c->g,
-                                                       (typename F::R)c->kappa, nrhs, mask);
+    k_dslash<F, O, 0><<<grid, DSLASH_TPB, 0, c->stream>>>((const char*)in, (char*)out, gauge, clover, c->g,
+                                                          (typename F::R)c->kappa, nrhs, mask);
   QCD_CUDA_OK(cudaGetLastError());
   return QCD_OK;
 }
@@ -78,12 +80,18 @@ qcd_status launch(qcd_ctx* c, const void* in, void* out, const void* gauge, cons
 // Algorithmic cost per site: each input spinor read once, the output written
 // once, the 4 links of the site and its clover term read once per launch;
 // 1320 flops for the eight spin-projected hops and 504 for the clover term.
+// out_prec = QCD_PREC_H16 (FP32 input only): the output is stored as FP16 with
+// a per-site scale.
 qcd_status dslash_apply(qcd_ctx* c, const void* in, void* out, int prec, int nrhs, int dagger, const int* mask,
-                        int nactive) {
+                        int nactive, int out_prec) {
   const double V = c->g.V;
   if (prec == QCD_PREC_F64) {
     ProfScope ps(c, FAM_DSLASH_D, V * (nactive * 2.0 * 192 + 4 * 144 + 576), V * nactive * 1824.0);
     return launch<FieldsD>(c, in, out, c->gaugeD.p, c->cloverD.p, nrhs, dagger, mask);
+  }
+  if (out_prec == QCD_PREC_H16) {
+    ProfScope ps(c, FAM_DSLASH_F, V * (nactive * (96.0 + FieldsH::spinor_bytes) + 4 * 48 + 288), V * nactive * 1824.0);
+    return launch<FieldsF, FieldsH>(c, in, out, c->gaugeF.p, c->cloverF.p, nrhs, dagger, mask);
   }
   ProfScope ps(c, FAM_DSLASH_F, V * (nactive * 2.0 * 96 + 4 * 48 + 288), V * nactive * 1824.0);
   return launch<FieldsF>(c, in, out, c->gaugeF.p, c->cloverF.p, nrhs, dagger, mask);

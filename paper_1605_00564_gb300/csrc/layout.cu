@@ -293,5 +293,5 @@ qcd_status layout_spinor_export(qcd_ctx* c, const void* in, double* out, int pre
 }
 
 size_t spinor_bytes(const qcd_ctx* c, int prec) {
-  return (size_t)c->g.V * (prec == QCD_PREC_F64 ? 192 : 96);
+  return (size_t)c->g.V * (prec == QCD_PREC_F64 ? 192 : prec == QCD_PREC_H16 ? FieldsH::spinor_bytes : 96);
 }

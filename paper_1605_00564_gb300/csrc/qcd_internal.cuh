@@ -11,6 +11,10 @@
 //   gauge  FP32   float4  [4][3][V]      rows 0 and 1; row 2 = conj(r0 x r1)
 //   clover FP64   double2 [36][V]        two packed 6x6 Hermitian chiral blocks
 //   clover FP32   float4  [18][V]        same 72 reals in groups of four
+//   spinor H16    uint2   [rhs][6][V] + float [rhs][V]: four FP16 values
+//                 (components 2k, 2k+1) per uint2, scaled so that the site's
+//                 largest real maps to 2^15, then the site's scale factor
+//                 (52 bytes per site; storage only, arithmetic in FP32)
 //
 // A packed Hermitian 6x6 block holds its 6 real diagonal entries followed by
 // the 15 complex entries below the diagonal in row order
@@ -20,6 +24,7 @@
 // the operator: A(x) = 1 + i kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -298,6 +303,68 @@ struct FieldsF {   // FP32
   static constexpr size_t spinor_bytes = 96, link_bytes = 48, clover_bytes = 288;
 };
 
+// Internal precision code of the FP16 + per-site scale storage (Krylov images
+// chi_k of the sloppy solves); never accepted at the C-ABI.
+constexpr int QCD_PREC_H16 = 2;
+
+__device__ inline unsigned h2_bits(__half2 h) { return *reinterpret_cast<unsigned*>(&h); }
+__device__ inline __half2 bits_h2(unsigned u) { return *reinterpret_cast<__half2*>(&u); }
+
+struct FieldsH {   // FP16 spinor storage with one FP32 scale per site
+  using R = float;
+  static constexpr float kTop = 32768.f;   // the site's largest |real| is stored as 2^15
+  static constexpr size_t spinor_bytes = 52;
+  static __device__ inline const float* scale_ptr(const void* base, int V) {
+    return (const float*)((const uint2*)base + 6 * (size_t)V);
+  }
+  // site value = scale * (FP16 word); encode and decode are the exact steps
+  // of a store and a later load, so a kernel can round in registers
+  static __device__ inline void encode(const Spinor<float>& o, uint2 (&w)[6], float& sc) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(o.c[k].re), fabsf(o.c[k].im)));
+    const float f = m > 0.f ? kTop / m : 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const __half2 a = __floats2half2_rn(f * o.c[2 * k].re, f * o.c[2 * k].im);
+      const __half2 b = __floats2half2_rn(f * o.c[2 * k + 1].re, f * o.c[2 * k + 1].im);
+      w[k] = make_uint2(h2_bits(a), h2_bits(b));
+    }
+    sc = m / kTop;
+  }
+  static __device__ inline Spinor<float> decode(const uint2 (&w)[6], float sc) {
+    Spinor<float> o;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float2 a = __half22float2(bits_h2(w[k].x)), b = __half22float2(bits_h2(w[k].y));
+      o.c[2 * k] = cmk(sc * a.x, sc * a.y);
+      o.c[2 * k + 1] = cmk(sc * b.x, sc * b.y);
+    }
+    return o;
+  }
+  static __device__ inline void load_words(const void* base, int V, int s, uint2 (&w)[6], float& sc) {
+    const uint2* p = (const uint2*)base;
+    sc = __ldg(scale_ptr(base, V) + s);
+#pragma unroll
+    for (int k = 0; k < 6; k++) w[k] = __ldg(p + (size_t)k * V + s);
+  }
+  static __device__ inline Spinor<float> load_spinor(const void* base, int V, int s) {
+    uint2 w[6];
+    float sc;
+    load_words(base, V, s, w, sc);
+    return decode(w, sc);
+  }
+  static __device__ inline void store_spinor(void* base, int V, int s, const Spinor<float>& o) {
+    uint2 w[6];
+    float sc;
+    encode(o, w, sc);
+    uint2* p = (uint2*)base;
+#pragma unroll
+    for (int k = 0; k < 6; k++) p[(size_t)k * V + s] = w[k];
+    ((float*)scale_ptr(base, V))[s] = sc;
+  }
+};
+
 // Apply one packed Hermitian 6x6 block (36 reals starting at cl[k0]) to v.
 template <typename R>
 __host__ __device__ inline void clover_block_apply(const R* cl, int k0, const Cplx<R>* v, Cplx<R>* out) {
@@ -407,9 +474,10 @@ qcd_status layout_spinor_export(qcd_ctx* c, const void* in, double* out, int pre
 qcd_status clover_export(qcd_ctx* c, double* out_dev);
 
 // out = D in (or D^+), internal layout, precision prec; mask may be null,
-// nactive = number of unmasked right-hand sides (for the timing records)
+// nactive = number of unmasked right-hand sides (for the timing records);
+// out_prec = QCD_PREC_H16 stores an FP32 operator's output as FP16 + scale
 qcd_status dslash_apply(qcd_ctx* c, const void* in, void* out, int prec, int nrhs, int dagger, const int* mask,
-                        int nactive);
+                        int nactive, int out_prec = -1);
 
 // reductions / vector ops (internal layouts; n = 12 V complex per rhs)
 qcd_status blas_norm2(qcd_ctx* c, const void* x, int prec, int nrhs, double* out_dev, const int* mask);
@@ -425,9 +493,10 @@ qcd_status blas_gs_dots(qcd_ctx* c, const void* chi, int prec, size_t jstride, i
                         const int* mask, int nactive);
 qcd_status blas_gs_orth(qcd_ctx* c, void* chi, int prec, size_t jstride, int k, const double* dots_dev,
                         const void* rho, int prho, int nrhs, double* n2c_dev, const int* mask, int nactive);
-// chi_k *= inv; rho -= ck chi_k, rho in the inner precision prec
-qcd_status blas_gs_finish_inner(qcd_ctx* c, void* chik, int prec, const double* inv_dev, const double* ck_dev,
-                                void* rho, int nrhs, double* rn2_dev, const int* mask, int nactive);
+// chi_k *= inv; rho -= ck chi_k; chi_k in precision pchi (F64, F32 or H16),
+// rho in the inner precision prho
+qcd_status blas_gs_finish_inner(qcd_ctx* c, void* chik, int pchi, const double* inv_dev, const double* ck_dev,
+                                void* rho, int prho, int nrhs, double* rn2_dev, const int* mask, int nactive);
 // out = x - y
 qcd_status blas_xmy(qcd_ctx* c, const void* x, const void* y, void* out, int prec, int nrhs, const int* mask);
 

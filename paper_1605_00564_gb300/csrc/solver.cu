@@ -52,9 +52,10 @@ struct Work {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-qcd_status get_work(qcd_ctx* c, int n, int nkv, int prec, Work& w) {
+qcd_status get_work(qcd_ctx* c, int n, int nkv, int prec, int pchi, Work& w) {
   const size_t VD = spinor_bytes(c, QCD_PREC_F64) * n;
   const size_t VI = spinor_bytes(c, prec) * n;
+  const size_t VC = align256(spinor_bytes(c, pchi) * n);
   DevBuf* bufD = c->wsD;
   QCD_TRY(devbuf_ensure(bufD[0], VD));
   QCD_TRY(devbuf_ensure(bufD[1], VD));
@@ -65,12 +66,12 @@ qcd_status get_work(qcd_ctx* c, int n, int nkv, int prec, Work& w) {
   w.rho = (char*)bufD[2].p;
   w.tmp = (char*)bufD[3].p;
   DevBuf& basis = prec == QCD_PREC_F64 ? c->basisD : c->basisF;
-  QCD_TRY(devbuf_ensure(basis, VI * (2 * nkv + 3)));
+  QCD_TRY(devbuf_ensure(basis, VI * (nkv + 3) + VC * nkv));
   w.rhoS = (char*)basis.p;
   w.delta = w.rhoS + VI;
   w.sapin = w.delta + VI;
   w.phi = w.sapin + VI;
-  w.chi = w.phi + VI * nkv;
+  w.chi = w.phi + VI * nkv;        // nkv vectors of VC bytes (chi's own storage)
   size_t sz = align256(sizeof(double2) * nkv * nkv * n) + align256(sizeof(double) * nkv * n) +
               2 * align256(sizeof(double) * n) + 2 * align256(sizeof(double2) * nkv * n) +
               align256(sizeof(double2) * 3 * n) + align256(sizeof(int) * n);
@@ -112,9 +113,12 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
   const qcd_solver_params& P = c->params;
   const int nkv = P.nkv, prec = P.precision;
   const bool use_dfl = P.dfl && dfl_ready(c) && prec == QCD_PREC_F32;
+  // storage of the Krylov images chi_k: FP16 + per-site scale with basis_half
+  const int pchi = (prec == QCD_PREC_F32 && P.basis_half) ? QCD_PREC_H16 : prec;
   Work w;
-  QCD_TRY(get_work(c, n, nkv, prec, w));
+  QCD_TRY(get_work(c, n, nkv, prec, pchi, w));
   const size_t VI = spinor_bytes(c, prec) * n;
+  const size_t VC = align256(spinor_bytes(c, pchi) * n);
   QCD_TRY(host_mirror(c, sizeof(double) * (8 * n + nkv * nkv * n * 2 + 4 * nkv * n * 2) + 64));
   double* h_rn2 = c->host_scal;
   double* h_eta = h_rn2 + n;
@@ -201,25 +205,25 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
       int nin_now = 0;
       for (int r = 0; r < n; r++) nin_now += incyc[r];
       char* phik = w.phi + VI * k;
-      char* chik = w.chi + VI * k;
+      char* chik = w.chi + VC * k;
       if (k == 0) QCD_TRY(blas_convert(c, w.rho, QCD_PREC_F64, w.rhoS, prec, n, w.mask));
       // SAP works in sapin; its first cycle reads the recursive residual rhoS
       if (use_dfl) {
         // deflated preconditioner: phi_k = Phi A^-1 Phi^+ rho + M_SAP(rho - D Phi A^-1 Phi^+ rho)
         QCD_TRY(dfl_low_mode(c, w.rhoS, phik, n, w.mask, nin_now, P.dfl_little_iters));
-        QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now));
-        QCD_TRY(blas_xmy(c, w.rhoS, chik, w.sapin, prec, n, w.mask));
+        QCD_TRY(dslash_apply(c, phik, w.delta, prec, n, 0, w.mask, nin_now));   // delta: scratch until the SAP
+        QCD_TRY(blas_xmy(c, w.rhoS, w.delta, w.sapin, prec, n, w.mask));
         QCD_TRY(sap_apply(c, w.sapin, phik, w.delta, prec, n, w.mask, nin_now, 1));
       } else {
         QCD_TRY(sap_apply(c, w.sapin, phik, w.delta, prec, n, w.mask, nin_now, 0, w.rhoS));
       }
-      QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now));
+      QCD_TRY(dslash_apply(c, phik, chik, prec, n, 0, w.mask, nin_now, pchi));
       // Gram-Schmidt against chi_0..chi_{k-1}, normalisation, residual update;
       // the update also writes the next preconditioner input rhoS
       double2* ak = w.a + (size_t)k * nkv * n;
-      QCD_TRY(blas_gs_dots(c, w.chi, prec, VI, k, n, (double*)ak, w.mask, nin_now));
+      QCD_TRY(blas_gs_dots(c, w.chi, pchi, VC, k, n, (double*)ak, w.mask, nin_now));
       // the recursive residual of the cycle is rhoS, in the inner precision
-      QCD_TRY(blas_gs_orth(c, w.chi, prec, VI, k, (const double*)ak, w.rhoS, prec, n, (double*)w.n2c, w.mask,
+      QCD_TRY(blas_gs_orth(c, w.chi, pchi, VC, k, (const double*)ak, w.rhoS, prec, n, (double*)w.n2c, w.mask,
                            nin_now));
       {
         ProfScope ps(c, FAM_BLAS, 0.0, 0.0);
@@ -227,7 +231,7 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
                                                           w.mask);
       }
       QCD_CUDA_OK(cudaGetLastError());
-      QCD_TRY(blas_gs_finish_inner(c, chik, prec, w.inv, (const double*)(w.cc + (size_t)k * n), w.rhoS, n,
+      QCD_TRY(blas_gs_finish_inner(c, chik, pchi, w.inv, (const double*)(w.cc + (size_t)k * n), w.rhoS, prec, n,
                                    (double*)w.rn2c, w.mask, nin_now));
       QCD_TRY(fetch(c, h_rn2c, w.rn2c, sizeof(double2) * n));
       for (int r = 0; r < n; r++) h_rn2[r] = h_rn2c[r].x;
@@ -290,7 +294,9 @@ int solver_tile(qcd_ctx* c, int nrhs) {
   if (P.rhs_tile > 0) return P.rhs_tile < nrhs ? P.rhs_tile : nrhs;
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
-  size_t per = 4 * spinor_bytes(c, QCD_PREC_F64) + (2 * (size_t)P.nkv + 2) * spinor_bytes(c, P.precision);
+  const int pchi = (P.precision == QCD_PREC_F32 && P.basis_half) ? QCD_PREC_H16 : P.precision;
+  size_t per = 4 * spinor_bytes(c, QCD_PREC_F64) + ((size_t)P.nkv + 3) * spinor_bytes(c, P.precision) +
+               (size_t)P.nkv * spinor_bytes(c, pchi);
   size_t budget = freeb > ((size_t)4 << 30) ? freeb - ((size_t)4 << 30) : freeb / 2;
   int t = (int)(budget / (per ? per : 1));
   if (t < 1) t = 1;

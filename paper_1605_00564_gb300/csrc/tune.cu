@@ -24,9 +24,10 @@ std::string tune_key(qcd_ctx* c, int nrhs, double tol) {
   cudaGetDevice(&dev);
   cudaGetDeviceProperties(&prop, dev);
   char buf[512];
-  snprintf(buf, sizeof(buf), "%dx%dx%dx%d k=%.6f csw=%.4f bc=%d prec=%d ncy=%d nmr=%d dfl=%d tol=%.1e n=%d gpu=%s",
-           c->dims[0], c->dims[1], c->dims[2], c->dims[3], c->kappa, c->csw, c->g.bc_t, c->params.precision,
-           c->params.ncy, c->params.nmr, c->params.dfl, tol, nrhs, prop.name);
+  snprintf(buf, sizeof(buf),
+           "%dx%dx%dx%d k=%.6f csw=%.4f bc=%d prec=%d bh=%d ncy=%d nmr=%d dfl=%d tol=%.1e n=%d gpu=%s", c->dims[0],
+           c->dims[1], c->dims[2], c->dims[3], c->kappa, c->csw, c->g.bc_t, c->params.precision,
+           c->params.basis_half, c->params.ncy, c->params.nmr, c->params.dfl, tol, nrhs, prop.name);
   for (char* p = buf; *p; p++)
     if (*p == '|' || *p == '\n') *p = '_';
   return buf;

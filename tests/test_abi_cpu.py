@@ -42,6 +42,14 @@ def test_host_only_calls(lib):
     p = qcd.SolverParams()
     lib.qcd_default_params(ctypes.byref(p))
     assert list(p.block) == [4, 4, 4, 4] and p.ncy == 5 and p.nmr == 4 and p.nkv == 16
+    # the binding's struct has the C struct's size: the library writes the last
+    # field and nothing beyond the binding's size
+    sz = ctypes.sizeof(qcd.SolverParams)
+    buf = (ctypes.c_ubyte * (sz + 64))(*([0xAB] * (sz + 64)))
+    q = qcd.SolverParams.from_buffer(buf)
+    lib.qcd_default_params(ctypes.byref(q))
+    assert q.graphs == 1 and q.basis_half == 0 and q.dfl_little_iters == 16
+    assert all(buf[i] == 0xAB for i in range(sz, sz + 64))
     assert lib.qcd_status_string(0) == b"ok"
     assert lib.qcd_status_string(4) == b"solver did not converge"
     # argument errors are reported before any device work

@@ -104,6 +104,32 @@ def test_solve_exact_and_sloppy(small, half):
     assert max(s["outer_iters"] for s in sts) < min(s["outer_iters"] for s in st)
 
 
+@pytest.mark.parametrize("tol", [1e-3, 1e-6, 1e-10])
+def test_solve_fp16_basis(small, tol):
+    """basis_half = 1: the images chi_k = D phi_k are stored as FP16 with a per-site
+    scale.  Every RHS still meets its tolerance in the FP64 true residual of the
+    oracle's operator; at the sloppy tolerance the FP16 rounding (about 3e-4
+    relative) costs at most a few iterations."""
+    lat, op, _ = small
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=1, dfl=0, basis_half=0)
+    src = synth.point_sources(lat.dims, (0, 0, 0, 0))
+    eta = to_dev(src)
+    try:
+        _, st32 = lat.solve(eta, tol)
+        lat.set_params(basis_half=1)
+        psi, st = lat.solve(eta, tol)
+    finally:
+        lat.set_params(basis_half=0)
+    psi = to_host(psi)
+    for r in range(12):
+        res = np.linalg.norm(src[r] - op.D(psi[r])) / np.linalg.norm(src[r])
+        assert st[r]["status"] == "QCD_OK" and res <= 1.05 * tol, (r, res, st[r])
+    it16 = sum(s["outer_iters"] for s in st)
+    it32 = sum(s["outer_iters"] for s in st32)
+    if tol >= 1e-3:
+        assert it16 <= 1.2 * it32 + 12, (it16, it32)
+
+
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
 def test_nucleon_contraction(small, prec, tol):
     from oracle import nucleon
@@ -155,15 +181,21 @@ def test_solve_multi_two_lattices():
         lat.close()
 
 
-def test_ama_estimate(small):
+@pytest.mark.parametrize("basis_half", [0, 1])
+def test_ama_estimate(small, basis_half):
     """qcd_ama_nucleon_2pt: the AMA combination equals eqs. caa1/caa2 (oracle) applied
     to the returned per-source correlators; the exact correlator equals an independent
-    exact solve + contraction; the sloppy ones track it at the solver tolerance."""
+    exact solve + contraction; the sloppy ones track it at the solver tolerance.  With
+    basis_half the sloppy solves use the FP16 Krylov basis, the exact ones FP32."""
     from oracle import nucleon
     lat, op, _ = small
-    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=1, dfl=0)
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=1, dfl=0,
+                   basis_half=basis_half)
     srcs = synth.ama_source_shifts(lat.dims, 2)
-    ama, allc, st = lat.ama_nucleon_2pt(srcs, 1, 1e-3, 1e-10)
+    try:
+        ama, allc, st = lat.ama_nucleon_2pt(srcs, 1, 1e-3, 1e-10)
+    finally:
+        lat.set_params(basis_half=0)
     assert all(s["status"] == "QCD_OK" for s in st)
     ref = nucleon.ama_combine(allc[:2], allc[2:3], allc[0:1])
     assert np.abs(ama - ref).max() <= 1e-14 * np.abs(ref).max()
