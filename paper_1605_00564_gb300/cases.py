@@ -7,6 +7,8 @@ L2 where DRAM figures matter).
     python -m paper_1605_00564_gb300.cases sap32       # same with FP32 block copies
     python -m paper_1605_00564_gb300.cases deflation   # deflation setup + one deflated sloppy solve, 16^3x32
     python -m paper_1605_00564_gb300.cases contract    # nucleon contraction, 16^3x32
+    python -m paper_1605_00564_gb300.cases gcr         # sloppy SAP-GCR solve, 16^3x32, 12 RHS, nkv 8, FP16 chi_k
+    python -m paper_1605_00564_gb300.cases gcr32       # same with FP32 chi_k
 """
 import os
 import sys
@@ -59,7 +61,17 @@ def contract():
         lat.nucleon_2pt(prop, (0, 0, 0, 0), precision=prec)
 
 
-CASES = {"dslash": dslash, "sap": sap, "sap32": lambda: sap(0), "deflation": deflation, "contract": contract}
+def gcr(basis_half=1):
+    import torch
+    from paper_1605_00564_gb300 import synth
+    lat = _lattice((32, 16, 16, 16), kappa=0.13)
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=8, sap_half=1, dfl=0, basis_half=basis_half)
+    eta = torch.from_numpy(synth.point_sources(lat.dims, (0, 0, 0, 0))).cuda()
+    lat.solve(eta, 1e-3)
+
+
+CASES = {"dslash": dslash, "sap": sap, "sap32": lambda: sap(0), "deflation": deflation, "contract": contract,
+         "gcr": gcr, "gcr32": lambda: gcr(0)}
 
 if __name__ == "__main__":
     import torch
