@@ -91,6 +91,10 @@ template <typename X, typename Y>
 struct Acc { using R = double; };
 template <>
 struct Acc<PF, PF> { using R = float; };
+template <>
+struct Acc<PH, PF> { using R = float; };
+template <>
+struct Acc<PH, PH> { using R = float; };
 
 __device__ inline double2 warp_sum(double2 v) {
 #pragma unroll
@@ -127,6 +131,7 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce(const char* __restrict__ x, 
     using R = typename Acc<X, Y>::R;
     const char* xb = x + (size_t)rhs * X::bytes * V;
     const char* yb = OP ? y + (size_t)rhs * Y::bytes * V : nullptr;
+    R tr = 0, ti = 0;   // per-thread sums, widened once
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
       R sr = 0, si = 0;
 #pragma unroll
@@ -142,9 +147,10 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce(const char* __restrict__ x, 
           si += (R)a.re * (R)c.im - (R)a.im * (R)c.re + (R)b.re * (R)d.im - (R)b.im * (R)d.re;
         }
       }
-      acc.x += (double)sr;
-      acc.y += (double)si;
+      tr += sr;
+      ti += si;
     }
+    acc = make_double2((double)tr, (double)ti);
   }
   double2 t = block_sum(acc);
   if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = t;
@@ -471,7 +477,11 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, s
   const size_t roff = (size_t)rhs * X::bytes * V;
   char* ckp = chi + k * jstride + roff;
   const char* rp = rho + (size_t)rhs * RH::bytes * V;
-  double n2 = 0, cr = 0, ci = 0;
+  // per-thread sums in the arithmetic type of the pair (FP32 unless FP64 is
+  // involved), widened to FP64 once per thread: FP64 arithmetic per site
+  // would make the pass ALU-bound on this GPU
+  using A = typename Acc<X, RH>::R;
+  A n2 = 0, cr = 0, ci = 0;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
     Cplx<R> a[12];
     ld_site<X>(ckp, V, s, a);
@@ -491,12 +501,16 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, s
     ld_site<RH>(rp, V, s, x);
 #pragma unroll
     for (int q = 0; q < 12; q++) {
-      n2 += (double)(a[q].re * a[q].re + a[q].im * a[q].im);
-      cr += (double)a[q].re * x[q].re + (double)a[q].im * x[q].im;
-      ci += (double)a[q].re * x[q].im - (double)a[q].im * x[q].re;
+      const A ar = (A)a[q].re, ai = (A)a[q].im, xr = (A)x[q].re, xi = (A)x[q].im;
+      n2 = rfma(ar, ar, n2);
+      n2 = rfma(ai, ai, n2);
+      cr = rfma(ar, xr, cr);
+      cr = rfma(ai, xi, cr);
+      ci = rfma(ar, xi, ci);
+      ci = rfma(-ai, xr, ci);
     }
   }
-  double v[3] = {n2, cr, ci};
+  double v[3] = {(double)n2, (double)cr, (double)ci};
   block_sum_n<3>(v, sh);
   if (threadIdx.x == 0) {
     double2* pp = part + (size_t)rhs * 2 * gridDim.x;
@@ -521,20 +535,28 @@ __global__ void __launch_bounds__(GS_TPB) k_caxpy_sm(char* __restrict__ y, const
   char* yb = y + (size_t)rhs * PD::bytes * V;
   const size_t xoff = (size_t)rhs * PF::bytes * V;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
-    Cplx<double> a[12];
+    // the combination sum_j coef_j x_j in FP32 (the x_j are FP32), then one
+    // FP64 add per component: FP64 multiply-adds per basis vector would make
+    // the pass ALU-bound on this GPU
+    Cplx<float> d[12];
 #pragma unroll
-    for (int q = 0; q < 6; q++) PD::ld(yb, V, q, s, a[2 * q], a[2 * q + 1]);
+    for (int q = 0; q < 12; q++) d[q] = cmk(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < KMAX; j++) {
       if (j < nx) {
         Cplx<float> u[12];
 #pragma unroll
         for (int q = 0; q < 6; q++) PF::ld(xbase + j * xstride + xoff, V, q, s, u[2 * q], u[2 * q + 1]);
-        const Cplx<double> w = cmk(c_s[j].x, c_s[j].y);
+        const Cplx<float> w = cmk((float)c_s[j].x, (float)c_s[j].y);
 #pragma unroll
-        for (int q = 0; q < 12; q++) a[q] = a[q] + w * cmk((double)u[q].re, (double)u[q].im);
+        for (int q = 0; q < 12; q++) cmac(d[q], w, u[q]);
       }
     }
+    Cplx<double> a[12];
+#pragma unroll
+    for (int q = 0; q < 6; q++) PD::ld(yb, V, q, s, a[2 * q], a[2 * q + 1]);
+#pragma unroll
+    for (int q = 0; q < 12; q++) a[q] = a[q] + cmk((double)d[q].re, (double)d[q].im);
 #pragma unroll
     for (int q = 0; q < 6; q++) PD::st(yb, V, q, s, a[2 * q], a[2 * q + 1]);
   }
@@ -554,7 +576,7 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_finish_inner(char* __restrict__ c
   char* rp = rho + (size_t)rhs * XR::bytes * V;
   const R f = (R)inv[rhs];
   const Cplx<R> mc = cmk((R)-ck[rhs].x, (R)-ck[rhs].y);
-  double n2 = 0;
+  R n2 = 0;   // per-thread sum, widened once (see k_gs_orth_sm)
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
     Cplx<R> a[12], x[12];
     ld_site<XR>(rp, V, s, x);
@@ -581,9 +603,9 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_finish_inner(char* __restrict__ c
       acc += x[q].re * x[q].re + x[q].im * x[q].im;
     }
     st_site<XR>(rp, V, s, x);
-    n2 += (double)acc;
+    n2 += acc;
   }
-  double v[1] = {n2};
+  double v[1] = {(double)n2};
   block_sum_n<1>(v, sh);
   if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = make_double2(v[0], 0.0);
 }

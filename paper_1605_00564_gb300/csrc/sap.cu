@@ -333,6 +333,51 @@ __device__ inline void smem_block_hop(Spinor<float>& p, const typename RStore<BF
   }
 }
 
+// One direction of the boundary gather with the block residual in shared
+// memory (FP32): every site on the +MU face and every site on the -MU face
+// (disjoint sets for b_MU >= 2) receives the hop from the neighbouring block's
+// delta.  One thread per face site, so all lanes of the busy warps work; the
+// site's residual is read, updated and written back by that thread, in the
+// same arithmetic as a per-site update.  co: the block's first site.
+template <int MU>
+__device__ inline void smem_gather_dir(Cplx<float>* r_s, const SapGeom& sg, const Geom& g, const char* delta,
+                                       const float4* gauge, const int co[4], int l, float kappa) {
+  const int nface = sg.vb / sg.b[MU];
+  if (l >= 2 * nface) return;
+  const bool fwd = l < nface;
+  int t = fwd ? l : l - nface;
+  int lc[4], c[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int nu = (k + 1) & 3;   // x, y, z, then t
+    if (nu == MU) {
+      lc[nu] = fwd ? sg.b[MU] - 1 : 0;
+    } else {
+      lc[nu] = t % sg.b[nu];
+      t /= sg.b[nu];
+    }
+  }
+  const int ls = lc[0] * sg.lst[0] + lc[1] * sg.lst[1] + lc[2] * sg.lst[2] + lc[3] * sg.lst[3];
+#pragma unroll
+  for (int mu = 0; mu < 4; mu++) c[mu] = co[mu] + lc[mu];
+  const int s = ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
+  Spinor<float> r = rs_load<false>(r_s, sg.vb, ls);
+  if (fwd) {
+    const int sf = site_fwd(g, s, c, MU);
+    const float sign = (MU == 0 && c[0] == g.L[0] - 1) ? (float)g.bc_t * kappa : kappa;
+    HalfSpinor<float> h = project<MU, -1>(FieldsF::load_spinor(delta, g.V, sf));
+    h = su3_mul(FieldsF::load_link(gauge, g.V, MU, s), h);
+    accum_recon<MU, -1>(r, h, sign);
+  } else {
+    const int sb = site_bwd(g, s, c, MU);
+    const float sign = (MU == 0 && c[0] == 0) ? (float)g.bc_t * kappa : kappa;
+    HalfSpinor<float> h = project<MU, +1>(FieldsF::load_spinor(delta, g.V, sb));
+    h = su3_dag_mul(FieldsF::load_link(gauge, g.V, MU, sb), h);
+    accum_recon<MU, +1>(r, h, sign);
+  }
+  rs_store<false>(r_s, sg.vb, ls, r);
+}
+
 // B4 = true: the block is 4^4, known at compile time, so every shared-memory
 // offset (component stride vb, neighbour strides) is an immediate.
 template <typename S, bool BF, bool B4, int MAXT, int MINB>
@@ -404,13 +449,33 @@ __global__ void __launch_bounds__(MAXT, MINB)
   for (int k = 0; k < 18; k++) cl_s[(size_t)k * vb + l] = Stage<S>::put(__ldg(clover + (size_t)k * g.V + s));
 
   Spinor<float> r = FieldsF::load_spinor(rho_src, g.V, s);
-  if (gather) {
-    face_hop<FieldsF, 0>(r, delta, sg, gauge, g, s, c, lc, kappa);
-    face_hop<FieldsF, 1>(r, delta, sg, gauge, g, s, c, lc, kappa);
-    face_hop<FieldsF, 2>(r, delta, sg, gauge, g, s, c, lc, kappa);
-    face_hop<FieldsF, 3>(r, delta, sg, gauge, g, s, c, lc, kappa);
+  if (BF) {
+    // bf16 shared residual: the site's own residual stays FP32 in registers
+    if (gather) {
+      face_hop<FieldsF, 0>(r, delta, sg, gauge, g, s, c, lc, kappa);
+      face_hop<FieldsF, 1>(r, delta, sg, gauge, g, s, c, lc, kappa);
+      face_hop<FieldsF, 2>(r, delta, sg, gauge, g, s, c, lc, kappa);
+      face_hop<FieldsF, 3>(r, delta, sg, gauge, g, s, c, lc, kappa);
+    }
+    rs_store<BF>(r_s, vb, l, r);
+  } else {
+    rs_store<BF>(r_s, vb, l, r);
+    if (gather) {
+      // boundary term in four rounds (one direction each, both faces at once)
+      Cplx<float>* rf = (Cplx<float>*)r_s;
+      const int co[4] = {c[0] - lc[0], c[1] - lc[1], c[2] - lc[2], c[3] - lc[3]};
+      __syncthreads();
+      smem_gather_dir<0>(rf, sg, g, delta, gauge, co, l, kappa);
+      __syncthreads();
+      smem_gather_dir<1>(rf, sg, g, delta, gauge, co, l, kappa);
+      __syncthreads();
+      smem_gather_dir<2>(rf, sg, g, delta, gauge, co, l, kappa);
+      __syncthreads();
+      smem_gather_dir<3>(rf, sg, g, delta, gauge, co, l, kappa);
+      __syncthreads();
+      r = rs_load<BF>(r_s, vb, l);
+    }
   }
-  rs_store<BF>(r_s, vb, l, r);
 
   Spinor<float> x;
 #pragma unroll
