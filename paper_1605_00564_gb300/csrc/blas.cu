@@ -70,17 +70,23 @@ __device__ inline void st_site<PH>(char* b, int V, int s, const Cplx<float> (&a)
   for (int q = 0; q < 12; q++) v.c[q] = a[q];
   FieldsH::store_spinor(b, V, s, v);
 }
-// a <- the values a later load of st_site(a) returns (identity except for PH)
+// store a, then a <- the values a later load returns (a changes only for PH)
 template <typename X>
-__device__ inline void round_site(Cplx<typename X::R> (&)[12]) {}
+__device__ inline void st_site_rounded(char* b, int V, int s, Cplx<typename X::R> (&a)[12]) {
+  st_site<X>(b, V, s, a);
+}
 template <>
-__device__ inline void round_site<PH>(Cplx<float> (&a)[12]) {
+__device__ inline void st_site_rounded<PH>(char* b, int V, int s, Cplx<float> (&a)[12]) {
   Spinor<float> v;
 #pragma unroll
   for (int q = 0; q < 12; q++) v.c[q] = a[q];
   uint2 w[6];
   float sc;
   FieldsH::encode(v, w, sc);
+  uint2* p = (uint2*)b;
+#pragma unroll
+  for (int k = 0; k < 6; k++) p[(size_t)k * V + s] = w[k];
+  ((float*)FieldsH::scale_ptr(b, V))[s] = sc;
   v = FieldsH::decode(w, sc);
 #pragma unroll
   for (int q = 0; q < 12; q++) a[q] = v.c[q];
@@ -495,8 +501,7 @@ __global__ void __launch_bounds__(GS_TPB) k_gs_orth_sm(char* __restrict__ chi, s
         for (int q = 0; q < 12; q++) cmac(a[q], mw, u[q]);
       }
     }
-    st_site<X>(ckp, V, s, a);
-    round_site<X>(a);   // the norm and the overlap with rho of chi_k as stored
+    st_site_rounded<X>(ckp, V, s, a);   // norm and overlap with rho of chi_k as stored
     Cplx<typename RH::R> x[12];
     ld_site<RH>(rp, V, s, x);
 #pragma unroll

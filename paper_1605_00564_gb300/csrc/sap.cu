@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
   RT* r_s = (RT*)smem_raw;
   CW* lk_s = (CW*)(smem_raw + (size_t)12 * vb * sizeof(RT));              // [4][9][vb]
   W* cl_s = (W*)(lk_s + (size_t)36 * vb);                                 // [18][vb]
-  __shared__ float red[3][32];
+  __shared__ float4 red[32];   // per warp: (p, r) re, im, (p, p)
 
   const int rhs = blockIdx.x % nrhs;   // RHS fastest, as in k_sap_sweep
   const int blk = blockIdx.x / nrhs;
@@ -501,19 +501,17 @@ __global__ void __launch_bounds__(MAXT, MINB)
     pr_re = warp_sum(pr_re);
     pr_im = warp_sum(pr_im);
     pp = warp_sum(pp);
-    if (lane == 0) {
-      red[0][warp] = pr_re;
-      red[1][warp] = pr_im;
-      red[2][warp] = pp;
-    }
+    if (lane == 0) red[warp] = make_float4(pr_re, pr_im, pp, 0.f);
     __syncthreads();
     float a_re = 0, a_im = 0, n2 = 0;
     for (int w = 0; w < nw; w++) {
-      a_re += red[0][w];
-      a_im += red[1][w];
-      n2 += red[2][w];
+      const float4 v = red[w];
+      a_re += v.x;
+      a_im += v.y;
+      n2 += v.z;
     }
-    Cplx<float> alpha = n2 > 0.f ? cmk(a_re / n2, a_im / n2) : cmk(0.f, 0.f);
+    const float inv_n2 = n2 > 0.f ? 1.f / n2 : 0.f;
+    Cplx<float> alpha = cmk(a_re * inv_n2, a_im * inv_n2);
     const Cplx<float> malpha = -alpha;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
