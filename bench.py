@@ -421,9 +421,12 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--basis-half", type=int, choices=(0, 1), default=None,
                     help="FP16+scale Krylov images in the sloppy solves (default: the workload's setting)")
+    ap.add_argument("--nkv", type=int, default=None, help="GCR restart length (default: the workload's)")
     args = ap.parse_args()
     if args.basis_half is not None:
         WORKLOAD["basis_half"] = args.basis_half
+    if args.nkv is not None:
+        WORKLOAD["nkv"] = args.nkv
     if args.impl == "reference":
         run_reference(args)
     else:
