@@ -313,6 +313,7 @@ __device__ inline __half2 bits_h2(unsigned u) { return *reinterpret_cast<__half2
 struct FieldsH {   // FP16 spinor storage with one FP32 scale per site
   using R = float;
   static constexpr float kTop = 32768.f;   // the site's largest |real| is stored as 2^15
+  static constexpr float kTiny = 1e-30f;
   static constexpr size_t spinor_bytes = 52;
   static __device__ inline const float* scale_ptr(const void* base, int V) {
     return (const float*)((const uint2*)base + 6 * (size_t)V);
@@ -323,14 +324,17 @@ struct FieldsH {   // FP16 spinor storage with one FP32 scale per site
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(o.c[k].re), fabsf(o.c[k].im)));
-    const float f = m > 0.f ? kTop / m : 0.f;
+    // sites whose largest |real| is below kTiny are stored as zero: 2^15 / m
+    // would overflow FP32 below about 1e-34, and such entries are negligible
+    // against any vector the solver normalises
+    const float f = m > kTiny ? kTop / m : 0.f;
 #pragma unroll
     for (int k = 0; k < 6; k++) {
       const __half2 a = __floats2half2_rn(f * o.c[2 * k].re, f * o.c[2 * k].im);
       const __half2 b = __floats2half2_rn(f * o.c[2 * k + 1].re, f * o.c[2 * k + 1].im);
       w[k] = make_uint2(h2_bits(a), h2_bits(b));
     }
-    sc = m / kTop;
+    sc = f > 0.f ? m / kTop : 0.f;
   }
   static __device__ inline Spinor<float> decode(const uint2 (&w)[6], float sc) {
     Spinor<float> o;

@@ -33,11 +33,18 @@ def test_dirac_fullsize(big):
     assert rel(to_host(lat.apply_dirac(to_dev(psi[None]), precision="f32"))[0], ref) < 2e-6
 
 
-@pytest.mark.parametrize("tol", [1e-10, 1e-3])
-def test_solve_fullsize(big, tol):
+@pytest.mark.parametrize("tol,basis_half", [(1e-10, 0), (1e-3, 0), (1e-3, 1)])
+def test_solve_fullsize(big, tol, basis_half):
+    """A point source at full size: far from it the SAP's block residuals and the
+    Krylov images reach FP32 denormals, which the MR step length and the FP16
+    encoding of chi_k must survive."""
     lat, op = big
     src = synth.point_source(lat.dims, (8, 16, 0, 0), 2, 1)
-    psi, st = lat.solve(to_dev(src[None]), tol)
+    lat.set_params(basis_half=basis_half)
+    try:
+        psi, st = lat.solve(to_dev(src[None]), tol)
+    finally:
+        lat.set_params(basis_half=0)
     res = np.linalg.norm(src - op.D(to_host(psi)[0])) / np.linalg.norm(src)
     assert st[0]["status"] == "QCD_OK" and res <= tol * 1.1, res
 
