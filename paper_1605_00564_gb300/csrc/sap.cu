@@ -336,32 +336,16 @@ __device__ inline void smem_block_hop(Spinor<float>& p, const typename RStore<BF
 // One direction of the boundary gather with the block residual in shared
 // memory (FP32): every site on the +MU face and every site on the -MU face
 // (disjoint sets for b_MU >= 2) receives the hop from the neighbouring block's
-// delta.  Each face site is handled by two threads, one per spin HS of the
-// projected half-spinor: e_MU pairs upper spin HS with exactly one lower spin
-// D(HS) (D = HS for MU = 0, 3; 1 - HS for MU = 1, 2), so the two threads read
-// half of the neighbour's delta each and update disjoint components of the
-// site's residual.  Per component the arithmetic is that of project,
-// su3_mul / su3_dag_mul and accum_recon.  co: the block's first site.
-template <int MU, int HS>
-__device__ inline Cplx<float> e_half(const Cplx<float> (&v)[3], int a) {   // (e_MU v)_HS, colour a
-  if (MU == 0) return -v[a];
-  if (MU == 1) return mul_mi(v[a]);                       // -i sigma_1: (e v)_HS = -i v_{1-HS}
-  if (MU == 2) return HS == 0 ? -v[a] : v[a];             // -i sigma_2: (e v)_0 = -v_1, (e v)_1 = v_0
-  return HS == 0 ? mul_mi(v[a]) : mul_i(v[a]);            // -i sigma_3
-}
-template <int MU, int HS>
-__device__ inline Cplx<float> edag_half(Cplx<float> h) {  // contribution of h_HS to (e^+ h)_{D(HS)}
-  if (MU == 0) return -h;
-  if (MU == 1) return mul_i(h);                           // i sigma_1
-  if (MU == 2) return HS == 0 ? -h : h;                   // i sigma_2: (e^+ h)_0 = h_1, (e^+ h)_1 = -h_0
-  return HS == 0 ? mul_i(h) : mul_mi(h);                  // i sigma_3
-}
-template <int MU, int HS>
-__device__ inline void smem_gather_task(Cplx<float>* r_s, const SapGeom& sg, const Geom& g, const char* delta,
-                                        const float4* gauge, const int co[4], int task, int nface, float kappa) {
-  constexpr int D = (MU == 1 || MU == 2) ? 1 - HS : HS;   // the lower spin paired with HS
-  const bool fwd = task < nface;
-  int t = fwd ? task : task - nface;
+// delta.  One thread per face site, so all lanes of the busy warps work; the
+// site's residual is read, updated and written back by that thread, in the
+// same arithmetic as a per-site update.  co: the block's first site.
+template <int MU>
+__device__ inline void smem_gather_dir(Cplx<float>* r_s, const SapGeom& sg, const Geom& g, const char* delta,
+                                       const float4* gauge, const int co[4], int l, float kappa) {
+  const int nface = sg.vb / sg.b[MU];
+  if (l >= 2 * nface) return;
+  const bool fwd = l < nface;
+  int t = fwd ? l : l - nface;
   int lc[4], c[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
@@ -377,76 +361,21 @@ __device__ inline void smem_gather_task(Cplx<float>* r_s, const SapGeom& sg, con
 #pragma unroll
   for (int mu = 0; mu < 4; mu++) c[mu] = co[mu] + lc[mu];
   const int s = ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
-  const int sn = fwd ? site_fwd(g, s, c, MU) : site_bwd(g, s, c, MU);
-  const bool wrap = MU == 0 && (fwd ? c[0] == g.L[0] - 1 : c[0] == 0);
-  const float sign = wrap ? (float)g.bc_t * kappa : kappa;
-  // the neighbour's delta: upper spin HS and lower spin D (3 colours each)
-  Cplx<float> up[3], dn[3];
-  {
-    const float4* dp = (const float4*)delta;
-    float cmp[12];
-#pragma unroll
-    for (int q = 0; q < 2; q++) {   // components 3 HS .. 3 HS + 2 lie in float4 words (3 HS) / 2 and the next
-      const float4 w = __ldg(dp + (size_t)((3 * HS) / 2 + q) * g.V + sn);
-      cmp[4 * q] = w.x; cmp[4 * q + 1] = w.y; cmp[4 * q + 2] = w.z; cmp[4 * q + 3] = w.w;
-    }
-    const int o = (3 * HS) & 1;     // offset of component 3 HS inside the first word
-#pragma unroll
-    for (int a = 0; a < 3; a++) up[a] = cmk(cmp[2 * (o + a)], cmp[2 * (o + a) + 1]);
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-      const float4 w = __ldg(dp + (size_t)((6 + 3 * D) / 2 + q) * g.V + sn);
-      cmp[4 * q] = w.x; cmp[4 * q + 1] = w.y; cmp[4 * q + 2] = w.z; cmp[4 * q + 3] = w.w;
-    }
-    const int od = (6 + 3 * D) & 1;
-#pragma unroll
-    for (int a = 0; a < 3; a++) dn[a] = cmk(cmp[2 * (od + a)], cmp[2 * (od + a) + 1]);
+  Spinor<float> r = rs_load<false>(r_s, sg.vb, ls);
+  if (fwd) {
+    const int sf = site_fwd(g, s, c, MU);
+    const float sign = (MU == 0 && c[0] == g.L[0] - 1) ? (float)g.bc_t * kappa : kappa;
+    HalfSpinor<float> h = project<MU, -1>(FieldsF::load_spinor(delta, g.V, sf));
+    h = su3_mul(FieldsF::load_link(gauge, g.V, MU, s), h);
+    accum_recon<MU, -1>(r, h, sign);
+  } else {
+    const int sb = site_bwd(g, s, c, MU);
+    const float sign = (MU == 0 && c[0] == 0) ? (float)g.bc_t * kappa : kappa;
+    HalfSpinor<float> h = project<MU, +1>(FieldsF::load_spinor(delta, g.V, sb));
+    h = su3_dag_mul(FieldsF::load_link(gauge, g.V, MU, sb), h);
+    accum_recon<MU, +1>(r, h, sign);
   }
-  // projection (1 -+ g_MU): forward hop minus, backward hop plus
-  Cplx<float> h[3];
-#pragma unroll
-  for (int a = 0; a < 3; a++) h[a] = fwd ? up[a] - e_half<MU, HS>(dn, a) : up[a] + e_half<MU, HS>(dn, a);
-  // colour multiply by U_MU(x) or U_MU(x - MU)^+
-  const SU3<float> U = FieldsF::load_link(gauge, g.V, MU, fwd ? s : sn);
-  Cplx<float> hp[3];
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    if (fwd) {
-      Cplx<float> acc = U.m[a][0] * h[0];
-      cmac(acc, U.m[a][1], h[1]);
-      cmac(acc, U.m[a][2], h[2]);
-      hp[a] = acc;
-    } else {
-      Cplx<float> acc = cdot(U.m[0][a], h[0]);
-      cmac_conj(acc, U.m[1][a], h[1]);
-      cmac_conj(acc, U.m[2][a], h[2]);
-      hp[a] = acc;
-    }
-  }
-  // reconstruction into the residual: upper spin HS and lower spin D
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    Cplx<float>& ru = r_s[(size_t)(3 * HS + a) * sg.vb + ls];
-    Cplx<float>& rd = r_s[(size_t)(6 + 3 * D + a) * sg.vb + ls];
-    Cplx<float> vu = ru, vd = rd;
-    vu = vu + sign * hp[a];
-    const Cplx<float> w = edag_half<MU, HS>(hp[a]);
-    vd = fwd ? vd - sign * w : vd + sign * w;
-    ru = vu;
-    rd = vd;
-  }
-}
-template <int MU>
-__device__ inline void smem_gather_dir(Cplx<float>* r_s, const SapGeom& sg, const Geom& g, const char* delta,
-                                       const float4* gauge, const int co[4], int l, float kappa) {
-  const int nface = sg.vb / sg.b[MU];
-  const int ntask = 2 * nface;                 // sites of both faces
-  for (int i = l; i < 2 * ntask; i += sg.vb) {   // two threads per site
-    if (i < ntask)
-      smem_gather_task<MU, 0>(r_s, sg, g, delta, gauge, co, i, nface, kappa);
-    else
-      smem_gather_task<MU, 1>(r_s, sg, g, delta, gauge, co, i - ntask, nface, kappa);
-  }
+  rs_store<false>(r_s, sg.vb, ls, r);
 }
 
 // B4 = true: the block is 4^4, known at compile time, so every shared-memory
