@@ -132,7 +132,7 @@ const char* qcd_status_string(qcd_status s);
 const char* qcd_last_error(void);
 
 /* Create a context for a lattice dims = {T, X, Y, Z} on the current CUDA
- * device.  cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * device (library plumbing; no counterpart in the paper).  cuda_stream is a cudaStream_t (NULL = legacy default stream).
  * Each extent must be >= 2; T*X*Y*Z < 2^31. */
 qcd_status qcd_create(qcd_ctx** out, const int dims[4], void* cuda_stream);
 void qcd_destroy(qcd_ctx* ctx);
@@ -144,14 +144,16 @@ void qcd_destroy(qcd_ctx* ctx);
 qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int U_on_device, double csw, double kappa,
                           int time_bc);
 
-/* Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
+/* The solver's tunables (Sec. 2.2 and the struct above).
+ * Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
  * restart_drop 1e-5, precision F32, rhs_tile 0, sap_half 0, dfl 1,
  * dfl_little_iters 16, dfl_gen_iters 0, graphs 1, basis_half 0. */
 void qcd_default_params(qcd_solver_params* p);
 qcd_status qcd_set_params(qcd_ctx* ctx, const qcd_solver_params* p);
 
-/* out = D in (dagger = 0) or D^+ in (dagger = 1) for nrhs canonical spinors
- * on the device, computed in the given precision (inputs are rounded to it;
+/* The operator of the Dirac equation D psi = eta (Sec. 2.2; O(a)-improved
+ * Wilson quarks): out = D in (dagger = 0) or D^+ in (dagger = 1) for nrhs
+ * canonical spinors on the device, computed in the given precision (inputs are rounded to it;
  * the output is written back in FP64).  in and out must not overlap. */
 qcd_status qcd_apply_dirac(qcd_ctx* ctx, const double* in, double* out, int nrhs, int dagger, int precision);
 
@@ -206,6 +208,7 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_ex
                                double exact_tol, double* corr_ama, double* corr_all, qcd_rhs_stats* stats);
 
 /* The site-diagonal part A(x) = 1 + i kappa c_sw sum sigma F of the operator
+ * (the O(a)-improvement (clover) term of Sec. 2.2's Wilson-clover operator)
  * as [site][chirality 2][6][6] complex FP64 (device), chirality block 0 acting
  * on spins 0,1 and block 1 on spins 2,3, index 3*(spin & 1) + colour. */
 qcd_status qcd_get_clover(qcd_ctx* ctx, double* out);
