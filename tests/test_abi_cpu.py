@@ -61,3 +61,30 @@ def test_host_only_calls(lib):
 def test_library_is_sm103a():
     from paper_1605_00564_gb300 import build
     assert "compute_103a,code=sm_103a" in build.ARCH
+
+
+def _c_struct_fields(header, name):
+    """Field names of `typedef struct { ... } name;` in declaration order."""
+    import re
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", header, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            m = re.search(r"(\w+)\s*(\[[^\]]*\])?\s*$", part.strip())
+            fields.append(m.group(1))
+    return fields
+
+
+def test_binding_structs_match_header():
+    """The ctypes structures list the C structures' fields in the same order."""
+    import os
+    from paper_1605_00564_gb300 import qcd
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    header = open(os.path.join(root, "include", "qcd.h")).read()
+    for cname, py in (("qcd_solver_params", qcd.SolverParams), ("qcd_rhs_stats", qcd.RhsStats),
+                      ("qcd_kernel_time", qcd.KernelTime)):
+        assert _c_struct_fields(header, cname) == [f[0] for f in py._fields_], cname
