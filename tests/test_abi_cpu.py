@@ -88,3 +88,25 @@ def test_binding_structs_match_header():
     for cname, py in (("qcd_solver_params", qcd.SolverParams), ("qcd_rhs_stats", qcd.RhsStats),
                       ("qcd_kernel_time", qcd.KernelTime)):
         assert _c_struct_fields(header, cname) == [f[0] for f in py._fields_], cname
+
+
+def test_argument_errors_before_device_work(lib):
+    """Entry points reject bad arguments before touching the device (runs without a GPU;
+    the pointers below are never dereferenced on these paths)."""
+    I4 = ctypes.c_int * 4
+    buf = (ctypes.c_double * 8)()
+    cases = [
+        ((I4(8, 8, 8, 8), -1, None, I4(0, 0, 0, 0), buf, 0), b"null"),
+        ((I4(8, 1, 8, 8), -1, buf, I4(0, 0, 0, 0), buf, 0), b"extent"),
+        ((I4(8, 8, 8, 8), -1, buf, I4(0, 9, 0, 0), buf, 0), b"outside"),
+        ((I4(8, 8, 8, 8), 0, buf, I4(0, 0, 0, 0), buf, 0), b"time_bc"),
+        ((I4(8, 8, 8, 8), -1, buf, I4(0, 0, 0, 0), buf, 7), b"precision"),
+        ((I4(512, 256, 256, 256), -1, buf, I4(0, 0, 0, 0), buf, 0), b"too large"),
+    ]
+    for args, msg in cases:
+        assert lib.qcd_nucleon_2pt_noalloc(*args, None) == 1, msg
+        assert msg in lib.qcd_last_error(), (msg, lib.qcd_last_error())
+    assert lib.qcd_solve_multi(None, 1, None, None, None, None, None) == 1
+    assert b"null" in lib.qcd_last_error()
+    for code in range(9):
+        assert lib.qcd_status_string(code)
