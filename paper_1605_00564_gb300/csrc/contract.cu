@@ -1,164 +1,14 @@
-// Nucleon two-point function (eq. Nop and the P+- projections of Sec. 2.3).
-//
-// N_alpha = eps^{abc} (u^a^T G d^b) u^c_alpha, G = C g5, C = g0 g2; with u = d
-// and one point-source propagator S (12x12 per site, S^{a a'}_{alpha alpha'}),
-// the Wick contractions give
-//   G(x) = eps^{abc} eps^{a'b'c'} { S^{cc'} tr[S^{aa'T} G S^{bb'} G']
-//                                   - S^{ca'} G'^T S^{bb'T} G^T S^{ac'} },
-// G' = g0 G^+ g0^T.  In the chiral basis G = diag(J, J), J = [[0,-1],[1,0]],
-// and G' = -G, so both are signed permutations: G_{b, b^1} = g(b) and
-// G'_{b^1, b} = g(b) with g(b) = -1 for even b, +1 for odd b.  Hence
-//   tr[S^{aa'T} G S^{bb'} G'] = sum_{b,b'} g(b) g(b') S^{aa'}_{b b'} S^{bb'}_{b^1 b'^1}
-//   (G'^T S^{bb'T} G^T)_{ij} = g(i) g(j) S^{bb'}_{j^1 i^1}
-// and with P+- = (1 +- g0)/2, tr[P+- Z] = (1/2) sum_l (Z_{ll} -+ Z_{l^2, l}).
-//
-// Layout: 6 threads per site, one per sink colour permutation (a,b,c), each
-// summing over the 6 source permutations.  A CTA covers NS consecutive sites
-// of one timeslice; the propagator of those sites is staged in shared memory
-// (the 144 complex entries of a site are read by its 6 threads).  The CTA's
-// sum over its sites is written to a partial; a second kernel sums the
-// partials of each timeslice in a fixed order, re-references the time to the
-// source and applies the boundary sign of wrapped sink times.
-#include "qcd_internal.cuh"
+// Nucleon two-point function (eq. Nop and the P+- projections of Sec. 2.3)
+// on a propagator in the internal FP64 spinor layout; the kernels and the
+// contraction formulas are in nucleon_kernels.cuh.
+#include "nucleon_kernels.cuh"
 
-namespace {
-
-__constant__ int c_perm[6][4] = {  // a, b, c, sign
-    {0, 1, 2, 1}, {1, 2, 0, 1}, {2, 0, 1, 1}, {0, 2, 1, -1}, {2, 1, 0, -1}, {1, 0, 2, -1}};
-
-template <typename R>
-__device__ inline Cplx<R> Sget(const Cplx<R>* S_s, int ns, int i, int al, int a, int alp, int ap) {
-  return S_s[((3 * al + a) * 12 + 3 * alp + ap) * ns + i];
-}
-
-template <typename R>
-__device__ inline R gsign(int b) { return (b & 1) ? (R)1 : (R)-1; }
-
-template <typename R>
-__global__ void k_nucleon(const double2* __restrict__ prop, int V, int ns, double2* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cplx<R>* S_s = (Cplx<R>*)smem_raw;
-  const int s0 = blockIdx.x * ns;
-  // stage: entry e = comp*12 + rhs of site s0 + i is prop[(rhs*12 + comp)*V + s0 + i]
-  for (int idx = threadIdx.x; idx < 144 * ns; idx += blockDim.x) {
-    int i = idx % ns, e = idx / ns;
-    int comp = e / 12, rhs = e - comp * 12;
-    double2 v = prop[((size_t)rhs * 12 + comp) * V + s0 + i];
-    S_s[e * ns + i] = cmk((R)v.x, (R)v.y);
-  }
-  __syncthreads();
-
-  const int i = threadIdx.x % ns;
-  const int pq = threadIdx.x / ns;   // sink permutation 0..5
-  const int a = c_perm[pq][0], b = c_perm[pq][1], c = c_perm[pq][2];
-  const R eps = (R)c_perm[pq][3];
-  Cplx<R> accp = cmk((R)0, (R)0), accm = cmk((R)0, (R)0);
-#pragma unroll 1
-  for (int q = 0; q < 6; q++) {
-    const int ap = c_perm[q][0], bp = c_perm[q][1], cp = c_perm[q][2];
-    const R ee = eps * (R)c_perm[q][3];
-    // T = tr[S^{aa'T} G S^{bb'} G']
-    Cplx<R> T = cmk((R)0, (R)0);
-#pragma unroll
-    for (int be = 0; be < 4; be++)
-#pragma unroll
-      for (int bq = 0; bq < 4; bq++) {
-        Cplx<R> x = Sget(S_s, ns, i, be, a, bq, ap) * Sget(S_s, ns, i, be ^ 1, b, bq ^ 1, bp);
-        T = T + (gsign<R>(be) * gsign<R>(bq)) * x;
-      }
-    // tr[P+- S^{cc'}]
-    Cplx<R> d = cmk((R)0, (R)0), o = cmk((R)0, (R)0);
-#pragma unroll
-    for (int l = 0; l < 4; l++) {
-      d = d + Sget(S_s, ns, i, l, c, l, cp);
-      o = o + Sget(S_s, ns, i, l ^ 2, c, l, cp);
-    }
-    Cplx<R> t1p = T * ((R)0.5 * (d - o)), t1m = T * ((R)0.5 * (d + o));
-    // Y = S^{ca'} M, M_{kj} = g(k) g(j) S^{bb'}_{j^1 k^1}
-    Cplx<R> Y[4][4];
-#pragma unroll
-    for (int ii = 0; ii < 4; ii++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        Cplx<R> y = cmk((R)0, (R)0);
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-          y = y + (gsign<R>(k) * gsign<R>(j)) * (Sget(S_s, ns, i, ii, c, k, ap) * Sget(S_s, ns, i, j ^ 1, b, k ^ 1, bp));
-        Y[ii][j] = y;
-      }
-    // tr[P+- Y S^{ac'}] = (1/2) sum_{l,k} (Y_{lk} -+ Y_{l^2 k}) S^{ac'}_{kl}
-    Cplx<R> zd = cmk((R)0, (R)0), zo = cmk((R)0, (R)0);
-#pragma unroll
-    for (int l = 0; l < 4; l++)
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        Cplx<R> sv = Sget(S_s, ns, i, k, a, l, cp);
-        zd = zd + Y[l][k] * sv;
-        zo = zo + Y[l ^ 2][k] * sv;
-      }
-    Cplx<R> t2p = (R)0.5 * (zd - zo), t2m = (R)0.5 * (zd + zo);
-    accp = accp + ee * (t1p - t2p);
-    accm = accm + ee * (t1m - t2m);
-  }
-  // CTA sum (fixed order): warp shuffles, then one warp over the warp sums
-  __shared__ double red[4][32];
-  double v[4] = {(double)accp.re, (double)accp.im, (double)accm.re, (double)accm.im};
-#pragma unroll
-  for (int k = 0; k < 4; k++)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  if (lane == 0)
-    for (int k = 0; k < 4; k++) red[k][w] = v[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[4] = {0, 0, 0, 0};
-    for (int ww = 0; ww < nw; ww++)
-      for (int k = 0; k < 4; k++) t[k] += red[k][ww];
-    part[2 * (size_t)blockIdx.x] = make_double2(t[0], t[1]);
-    part[2 * (size_t)blockIdx.x + 1] = make_double2(t[2], t[3]);
-  }
-}
-
-// one CTA per timeslice: corr[p][trel] = sign * sum of the partials of timeslice t
-__global__ void k_nucleon_final(const double2* __restrict__ part, int per_t, int T, int t0, int bc3,
-                                double2* __restrict__ corr) {
-  const int t = blockIdx.x;
-  __shared__ double2 sh[2][256];
-  double2 ap = make_double2(0, 0), am = make_double2(0, 0);
-  for (int k = threadIdx.x; k < per_t; k += blockDim.x) {
-    double2 p = part[2 * ((size_t)t * per_t + k)], m = part[2 * ((size_t)t * per_t + k) + 1];
-    ap.x += p.x; ap.y += p.y; am.x += m.x; am.y += m.y;
-  }
-  sh[0][threadIdx.x] = ap;
-  sh[1][threadIdx.x] = am;
-  __syncthreads();
-  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st) {
-      sh[0][threadIdx.x].x += sh[0][threadIdx.x + st].x; sh[0][threadIdx.x].y += sh[0][threadIdx.x + st].y;
-      sh[1][threadIdx.x].x += sh[1][threadIdx.x + st].x; sh[1][threadIdx.x].y += sh[1][threadIdx.x + st].y;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    int trel = (t - t0 + T) % T;
-    double sg = (t < t0) ? (double)bc3 : 1.0;
-    corr[trel] = make_double2(sg * sh[0][0].x, sg * sh[0][0].y);
-    corr[T + trel] = make_double2(sg * sh[1][0].x, sg * sh[1][0].y);
-  }
-}
-
-}  // namespace
-
-// sites per CTA: the largest power of two <= 32 dividing the spatial volume
 int contract_sites_per_cta(const qcd_ctx* c) {
-  int L3 = c->g.L[1] * c->g.L[2] * c->g.L[3];
-  int ns = 32;
-  while (L3 % ns) ns >>= 1;
-  return ns;
+  return nucleon::sites_per_cta((long long)c->g.L[1] * c->g.L[2] * c->g.L[3]);
 }
 
 // corr_dev: [2][T] double2.  prop: 12 FP64 internal spinors (rhs = 3 spin + colour).
+// partials: at least 2 V / ns double2.
 qcd_status contract_nucleon(qcd_ctx* c, const void* prop, int t0, double* corr_dev, int precision,
                             double2* partials) {
   const int ns = contract_sites_per_cta(c);
@@ -166,20 +16,23 @@ qcd_status contract_nucleon(qcd_ctx* c, const void* prop, int t0, double* corr_d
   const int T = c->g.L[0];
   const int per_t = nb / T;
   const int bc3 = c->g.bc_t * c->g.bc_t * c->g.bc_t;
+  const int threads = nucleon::cta_threads(ns);
   // algorithmic cost per site: the 144 complex propagator entries read once;
   // 36 colour-permutation pairs x (16 + 64 + 32) complex multiply-adds
   ProfScope ps(c, FAM_CONTRACT, (double)c->g.V * 144 * 16, (double)c->g.V * 36 * 112 * 8, 2);
   if (precision == QCD_PREC_F64) {
-    size_t smem = (size_t)144 * ns * sizeof(Cplx<double>);
-    QCD_CUDA_OK(cudaFuncSetAttribute(k_nucleon<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_nucleon<double><<<nb, 6 * ns, smem, c->stream>>>((const double2*)prop, c->g.V, ns, partials);
+    const size_t smem = (size_t)144 * ns * sizeof(Cplx<double>);
+    QCD_CUDA_OK(cudaFuncSetAttribute(nucleon::k_sites<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    nucleon::k_sites<double, false><<<nb, threads, smem, c->stream>>>((const double2*)prop, c->g.V, ns, partials);
   } else {
-    size_t smem = (size_t)144 * ns * sizeof(Cplx<float>);
-    QCD_CUDA_OK(cudaFuncSetAttribute(k_nucleon<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_nucleon<float><<<nb, 6 * ns, smem, c->stream>>>((const double2*)prop, c->g.V, ns, partials);
+    const size_t smem = (size_t)144 * ns * sizeof(Cplx<float>);
+    QCD_CUDA_OK(cudaFuncSetAttribute(nucleon::k_sites<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    nucleon::k_sites<float, false><<<nb, threads, smem, c->stream>>>((const double2*)prop, c->g.V, ns, partials);
   }
   QCD_CUDA_OK(cudaGetLastError());
-  k_nucleon_final<<<T, 256, 0, c->stream>>>(partials, per_t, T, t0, bc3, (double2*)corr_dev);
+  nucleon::k_timeslices<<<T, 256, 0, c->stream>>>(partials, per_t, T, t0, bc3, (double2*)corr_dev);
   QCD_CUDA_OK(cudaGetLastError());
   return QCD_OK;
 }

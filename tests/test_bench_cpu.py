@@ -31,10 +31,10 @@ def test_roofline_record():
     assert pk["hbm_gbs"] > 0
     prof = {"sap_f32": {"ms": 2000.0, "bytes": 4e12, "flops": 8e13, "launches": 1000},
             "blas": {"ms": 500.0, "bytes": 3e12, "flops": 1e11, "launches": 4000}}
-    r = bench.roofline(prof, 3000.0, {"sm_mhz": 2070.0}, pk)
+    r = bench.roofline(prof, 3000.0, {"sm_mhz": 2070.0}, pk, sms=152)
     assert r["kernel"] == "sap_f32" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - 40.0) < 1e-6 and abs(r["share_of_step"] - 0.667) < 1e-3
     assert r["algorithmic_bytes_per_launch"] == 4_000_000_000
     prof["sap_f32"]["flops"] = 1e12        # below the ridge: HBM-bound
-    r = bench.roofline(prof, 3000.0, None, pk)
+    r = bench.roofline(prof, 3000.0, None, pk, sms=152)
     assert r["bound"] == "hbm" and abs(r["achieved"] - 2000.0) < 1e-6

@@ -1,21 +1,26 @@
 """CUDA path vs the FP64 oracle, element by element, through the C-ABI.
 
-Tolerances (norm-wise relative unless stated):
-  FP64 operator        1e-13   (same formula, different summation order)
-  FP32 operator        2e-6    (single-precision rounding of ~20 terms)
+Element-wise errors are |a_i - b_i| / max(|b_i|, rms(b)) (gpu_util.elem_err);
+each field is also checked on its own on the sites where a defect could hide
+(the time boundary of the operator, the block faces of the SAP).  Bounds:
+  FP64 operator        1e-12   (~100 rounded terms per element, 1.1e-16 each)
+  FP32 operator        1e-5    (the same with 6e-8 per term)
   clover term, FP64    1e-14   (max abs)
-  SAP FP64 vs oracle   1e-11   (identical MR algorithm in FP64)
-  SAP FP32 vs oracle   2e-4    (MR step lengths in FP32)
-  SAP FP32, 16-bit block copies of links/clover: 5e-3 (rounding of the copies)
-  SAP FP32, 16-bit copies + bf16 shared residual: 3e-2
-  exact solve          oracle-computed residual <= 1.1e-10, solution <= 1e-8
-  sloppy solve         oracle-computed residual <= 1e-3
-  contraction FP64     1e-12 of max |C|; FP32 2e-5 of max |C|
+  SAP FP64 vs oracle   1e-10   (identical MR algorithm in FP64)
+  SAP FP32 vs oracle   2e-3    (MR step lengths in FP32, three cycles)
+  SAP FP32, 16-bit block copies of links/clover: 3e-2 (rounding of the copies, 4.9e-4 each)
+  SAP FP32, 16-bit copies + bf16 shared residual: 2e-1 (bf16 rounding, 3.9e-3 each)
+  exact solve, every RHS: oracle-computed residual <= 1.1e-10; solution vs the
+                       oracle's 1e-13 solve: 1e-8 norm-wise (the stated bound),
+                       1e-7 element-wise
+  sloppy solve         oracle-computed residual <= 1e-3, every RHS
+  contraction          per timeslice, relative to |C(t)|: FP64 1e-12, FP32 2e-5
 """
 import numpy as np
 import pytest
 
-from gpu_util import make_lattice, rel, to_dev, to_host
+from gpu_util import (elem_err, elem_err_faces, make_lattice, oracle_solve_many, record, rel, timeslice_err, to_dev,
+                      to_host)
 from paper_1605_00564_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +44,10 @@ def test_dirac_fp64(request, which, dagger):
     psi = synth.random_spinor(lat.dims, 3, nrhs=3)
     out = to_host(lat.apply_dirac(to_dev(psi), dagger=dagger, precision="f64"))
     ref = np.stack([op.D(p, dagger=dagger) for p in psi])
-    assert rel(out, ref) < 1e-13
+    assert record("dirac_f64_%s_%d" % (which, dagger), elem_err(out, ref)) < 1e-12
+    # the time boundary (antiperiodic hops) on its own
+    edge = [0, lat.T - 1]
+    assert elem_err(out[:, edge], ref[:, edge]) < 1e-12
 
 
 @pytest.mark.parametrize("which", ["small", "ragged"])
@@ -48,14 +56,16 @@ def test_dirac_fp32(request, which):
     psi = synth.random_spinor(lat.dims, 4, nrhs=2)
     out = to_host(lat.apply_dirac(to_dev(psi), precision="f32"))
     ref = np.stack([op.D(p) for p in psi])
-    assert rel(out, ref) < 2e-6
+    assert record("dirac_f32_%s" % which, elem_err(out, ref)) < 1e-5
+    edge = [0, lat.T - 1]
+    assert elem_err(out[:, edge], ref[:, edge]) < 1e-5
 
 
 def test_dirac_periodic_time():
     lat, op, _ = make_lattice((4, 4, 4, 6), eps=0.3, csw=1.0, kappa=0.125, seed=5, bc_t=1)
     psi = synth.random_spinor(lat.dims, 9)
     out = to_host(lat.apply_dirac(to_dev(psi[None]), precision="f64"))[0]
-    assert rel(out, op.D(psi)) < 1e-13
+    assert record("dirac_f64_periodic", elem_err(out, op.D(psi))) < 1e-12
 
 
 def test_clover_field(small):
@@ -67,7 +77,7 @@ def test_clover_field(small):
     assert np.abs(ref[..., :6, 6:]).max() == 0.0
 
 
-@pytest.mark.parametrize("prec,half,tol", [("f64", 0, 1e-11), ("f32", 0, 2e-4), ("f32", 1, 5e-3), ("f32", 2, 3e-2)])
+@pytest.mark.parametrize("prec,half,tol", [("f64", 0, 1e-10), ("f32", 0, 2e-3), ("f32", 1, 3e-2), ("f32", 2, 2e-1)])
 @pytest.mark.parametrize("block", [(4, 4, 4, 4), (8, 4, 4, 4), (4, 2, 4, 2)])
 def test_sap_matches_oracle(small, prec, half, tol, block):
     from oracle.sap import SAP
@@ -77,15 +87,25 @@ def test_sap_matches_oracle(small, prec, half, tol, block):
     out = to_host(lat.apply_sap(to_dev(eta), precision=prec))
     s = SAP(op, block, ncy=3, nmr=4)
     ref = np.stack([s.apply(e) for e in eta])
-    assert rel(out, ref) < tol
+    name = "sap_%s_h%d_%s" % (prec, half, "x".join(map(str, block)))
+    assert record(name, elem_err(out, ref)) < tol
+    assert record(name + "_faces", elem_err_faces(out, ref, lat.dims, block)) < tol
+
+
+@pytest.fixture(scope="module")
+def oracle_solutions(small):
+    """The oracle's solutions of the 12 point sources at the origin (GCR to 1e-13)."""
+    lat, op, U = small
+    cfg = synth.CONFIGS["small_8c16"]
+    src = synth.point_sources(lat.dims, (0, 0, 0, 0))
+    return src, oracle_solve_many(U, cfg["kappa"], cfg["csw"], -1, src, tol=1e-13)
 
 
 @pytest.mark.parametrize("half", [0, 1, 2])
-def test_solve_exact_and_sloppy(small, half):
-    from oracle.solve import gcr
+def test_solve_exact_and_sloppy(small, oracle_solutions, half):
     lat, op, _ = small
     lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, precision="f32", sap_half=half)
-    src = synth.point_sources(lat.dims, (0, 0, 0, 0))
+    src, x = oracle_solutions
     eta = to_dev(src)
     psi, st = lat.solve(eta, 1e-10)
     psi = to_host(psi)
@@ -93,8 +113,8 @@ def test_solve_exact_and_sloppy(small, half):
         res = np.linalg.norm(src[r] - op.D(psi[r])) / np.linalg.norm(src[r])
         assert st[r]["status"] == "QCD_OK"
         assert res <= 1.1e-10, (r, res, st[r])
-    x, it, res = gcr(op, src[0], tol=1e-13)
-    assert rel(psi[0], x) < 1e-8
+        assert record("solve_exact_h%d_norm" % half, rel(psi[r], x[r])) < 1e-8, r
+        assert record("solve_exact_h%d_elem" % half, elem_err(psi[r], x[r])) < 1e-7, r
     psis, sts = lat.solve(eta, 1e-3)
     psis = to_host(psis)
     for r in range(12):
@@ -139,7 +159,20 @@ def test_nucleon_contraction(small, prec, tol):
     src = (3, 4, 0, 4)
     out = lat.nucleon_2pt(to_dev(prop), src, precision=prec)
     ref = nucleon.two_point(prop, src[0])
-    assert np.abs(out - ref).max() <= tol * np.abs(ref).max()
+    assert record("contract_random_%s" % prec, timeslice_err(out, ref)) <= tol
+
+
+def test_nucleon_contraction_solved(small, oracle_solutions):
+    """On the oracle's point-source propagator, whose correlator falls by
+    orders of magnitude from the source to the middle of the lattice: every
+    timeslice relative to itself (FP64)."""
+    from oracle import nucleon
+    lat, op, _ = small
+    _, x = oracle_solutions
+    out = lat.nucleon_2pt(to_dev(x), (0, 0, 0, 0), precision="f64")
+    ref = nucleon.two_point(x, 0)
+    assert np.abs(ref[0]).max() / np.abs(ref[0]).min() > 1e3          # the decay the check spans
+    assert record("contract_solved_f64", timeslice_err(out, ref)) <= 1e-12
 
 
 def test_autotune_and_cache(small, tmp_path):

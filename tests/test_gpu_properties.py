@@ -14,7 +14,7 @@
 import numpy as np
 import pytest
 
-from gpu_util import make_lattice, rel, to_dev, to_host
+from gpu_util import make_lattice, record, to_dev, to_host
 from paper_1605_00564_gb300 import synth
 from paper_1605_00564_gb300.qcd import QcdError
 
@@ -61,12 +61,12 @@ def test_translation_covariance_block_preserving():
         return (np.abs(cg[0] - c0[0]) / np.abs(c0[0]))[:8].max()
 
     # shift by (2, 1, 0, 1) blocks: Omega -> Omega, Omega* -> Omega*
-    d_even = delta((8, 4, 0, 4))
+    d_even = record("covariance_d_even", delta((8, 4, 0, 4)))
     assert d_even < 1e-4, d_even
     # shift by (1, 1, 0, 1) blocks exchanges Omega and Omega*: M_SAP changes
-    d_odd = delta((4, 4, 0, 4))
+    d_odd = record("covariance_d_odd", delta((4, 4, 0, 4)))
     # shift by one site: the blocks are not mapped onto blocks
-    d_site = delta((1, 0, 0, 0))
+    d_site = record("covariance_d_site", delta((1, 0, 0, 0)))
     assert d_odd > 10 * d_even and d_site > 10 * d_even, (d_even, d_odd, d_site)
 
 
