@@ -31,7 +31,7 @@ def test_dirac_fullsize(big):
     psi = synth.random_spinor(lat.dims, 81)
     ref = op.D(psi)
     edge = [0, lat.T - 1]
-    for prec, tol in (("f64", 1e-12), ("f32", 1e-5)):
+    for prec, tol in (("f64", 1e-13), ("f32", 5e-6)):
         out = to_host(lat.apply_dirac(to_dev(psi[None]), precision=prec))[0]
         assert record("dirac_fullsize_" + prec, elem_err(out, ref)) < tol
         assert elem_err(out[edge, :], ref[edge, :]) < tol

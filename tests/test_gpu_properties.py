@@ -61,13 +61,15 @@ def test_translation_covariance_block_preserving():
         return (np.abs(cg[0] - c0[0]) / np.abs(c0[0]))[:8].max()
 
     # shift by (2, 1, 0, 1) blocks: Omega -> Omega, Omega* -> Omega*
+    # measured: 0 (the shifted problem gives the same bits at t < 8)
     d_even = record("covariance_d_even", delta((8, 4, 0, 4)))
-    assert d_even < 1e-4, d_even
+    assert d_even < 1e-12, d_even
     # shift by (1, 1, 0, 1) blocks exchanges Omega and Omega*: M_SAP changes
     d_odd = record("covariance_d_odd", delta((4, 4, 0, 4)))
     # shift by one site: the blocks are not mapped onto blocks
     d_site = record("covariance_d_site", delta((1, 0, 0, 0)))
-    assert d_odd > 10 * d_even and d_site > 10 * d_even, (d_even, d_odd, d_site)
+    # measured 9.3e-3 and 2.7e-3: the sloppy solution differs at the level of its tolerance
+    assert d_odd > 1e-5 and d_site > 1e-5, (d_even, d_odd, d_site)
 
 
 def test_failure_paths(small):
