@@ -159,6 +159,23 @@ class Lattice:
         self.time_bc = -1
 
     # ----------------------------------------------------------------------
+    def _after_torch(self):
+        """The library works on self.stream; tensors handed to it were written on
+        torch's current stream (e.g. the zero-filled solution of solve): make
+        self.stream wait for that work before the call."""
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _before_torch(self):
+        """Results the library wrote on self.stream: make torch's current stream
+        wait for them (calls that return to the host have synchronised already)."""
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+
     def close(self):
         if self._ctx:
             _lib.qcd_destroy(self._ctx)
@@ -181,6 +198,7 @@ class Lattice:
         self.time_bc = int(time_bc)
         if isinstance(U, torch.Tensor):
             U = U.contiguous()
+            self._after_torch()
             st = _lib.qcd_load_gauge(self._ctx, _dev_ptr(U), 1, float(csw), float(kappa), int(time_bc))
         else:
             U = np.ascontiguousarray(U, dtype=np.complex128)
@@ -207,7 +225,9 @@ class Lattice:
         psi = psi.contiguous()
         n = psi.shape[0] if psi.dim() == 7 else 1
         out = torch.empty_like(psi)
+        self._after_torch()
         _check(_lib.qcd_apply_dirac(self._ctx, _dev_ptr(psi), _dev_ptr(out), n, int(bool(dagger)), PREC[precision]))
+        self._before_torch()
         return out
 
     def apply_sap(self, eta, precision="f32"):
@@ -215,7 +235,9 @@ class Lattice:
         eta = eta.contiguous()
         n = eta.shape[0] if eta.dim() == 7 else 1
         out = torch.empty_like(eta)
+        self._after_torch()
         _check(_lib.qcd_apply_sap(self._ctx, _dev_ptr(eta), _dev_ptr(out), n, PREC[precision]))
+        self._before_torch()
         return out
 
     def autotune(self, eta, tol, cache_path=None):
@@ -224,6 +246,7 @@ class Lattice:
         n = eta.shape[0] if eta.dim() == 7 else 1
         best = SolverParams()
         cp = cache_path.encode() if cache_path else None
+        self._after_torch()
         _check(_lib.qcd_autotune(self._ctx, _dev_ptr(eta), n, float(tol), cp, ctypes.byref(best)))
         self.params = best
         return {"block": list(best.block), "sap_half": best.sap_half, "nkv": best.nkv, "rhs_tile": best.rhs_tile}
@@ -237,7 +260,9 @@ class Lattice:
         psi = torch.zeros_like(eta) if psi0 is None else psi0.clone().contiguous()
         tols = (ctypes.c_double * n)(*([float(tol)] * n if np.isscalar(tol) else [float(x) for x in tol]))
         stats = (RhsStats * n)()
+        self._after_torch()
         st = _lib.qcd_solve(self._ctx, _dev_ptr(eta), _dev_ptr(psi), n, tols, stats)
+        self._before_torch()
         if check:
             _check(st, allow=(4,) if allow_not_converged else ())
         return psi, [s.as_dict() for s in stats]
@@ -246,6 +271,7 @@ class Lattice:
         """C[parity, t] (complex, host numpy) from a 12-spinor point-source propagator."""
         prop = prop.contiguous()
         out = np.zeros((2, self.T, 2), dtype=np.float64)
+        self._after_torch()
         _check(_lib.qcd_nucleon_2pt(self._ctx, _dev_ptr(prop), (ctypes.c_int * 4)(*src),
                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), PREC[precision]))
         return out[..., 0] + 1j * out[..., 1]
@@ -280,13 +306,16 @@ class Lattice:
     def deflation_setup(self, init, n_inv):
         """Build the deflation subspace from init (CUDA complex128, (ns,)+spinor shape)."""
         init = init.contiguous()
+        self._after_torch()
         _check(_lib.qcd_deflation_setup(self._ctx, _dev_ptr(init), int(init.shape[0]), int(n_inv)))
         self.dfl_ns = int(init.shape[0])
 
     def deflation_fields(self):
         import torch
         out = torch.empty(self.spinor_shape(self.dfl_ns), dtype=torch.complex128, device="cuda")
+        self._after_torch()
         _check(_lib.qcd_deflation_fields(self._ctx, _dev_ptr(out)))
+        self._before_torch()
         return out
 
     def n_blocks(self):
@@ -317,6 +346,7 @@ class Lattice:
         prop = torch.empty(self.spinor_shape(12), dtype=torch.complex128, device="cuda")
         corr = np.zeros((2, self.T, 2))
         stats = (RhsStats * 12)()
+        self._after_torch()
         _check(_lib.qcd_fh_forward(self._ctx, (ctypes.c_int * 4)(*src), float(tol), _dev_ptr(prop),
                                    corr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats))
         return prop, corr
@@ -326,6 +356,7 @@ class Lattice:
         g = np.ascontiguousarray(gcorr, dtype=np.float64)
         grad = np.zeros(2)
         stats = (RhsStats * 24)()
+        self._after_torch()
         _check(_lib.qcd_fh_gradient(self._ctx, _dev_ptr(prop.contiguous()), (ctypes.c_int * 4)(*src),
                                     g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol),
                                     grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats))
@@ -335,7 +366,9 @@ class Lattice:
         """A(x) as a CUDA complex128 tensor [V, 2, 6, 6]."""
         import torch
         out = torch.empty((self.V, 2, 6, 6), dtype=torch.complex128, device="cuda")
+        self._after_torch()
         _check(_lib.qcd_get_clover(self._ctx, _dev_ptr(out)))
+        self._before_torch()
         return out
 
 
@@ -351,6 +384,8 @@ def solve_multi(lattices, etas, tol):
     tols = [(ctypes.c_double * k)(*([float(tol)] * k)) for k in nr]
     stats = [(RhsStats * k)() for k in nr]
     VP = ctypes.c_void_p
+    for lat in lattices:
+        lat._after_torch()
     st = L.qcd_solve_multi((VP * n)(*[l._ctx for l in lattices]), n, (VP * n)(*[e.data_ptr() for e in etas]),
                            (VP * n)(*[p.data_ptr() for p in psis]), (ctypes.c_int * n)(*nr),
                            (ctypes.POINTER(ctypes.c_double) * n)(*[ctypes.cast(t, ctypes.POINTER(ctypes.c_double)) for t in tols]),

@@ -83,14 +83,18 @@ def test_clover_field(small):
 @pytest.mark.parametrize("prec,half,tol", [("f64", 0, 1e-13), ("f32", 0, 1e-5), ("f32", 1, 5e-3), ("f32", 2, 2e-2)])
 @pytest.mark.parametrize("block", [(4, 4, 4, 4), (8, 4, 4, 4), (4, 2, 4, 2)])
 def test_sap_matches_oracle(small, prec, half, tol, block):
+    _sap_vs_oracle(small, prec, half, tol, block)
+
+
+def _sap_vs_oracle(small, prec, half, tol, block, nrhs=2):
     from oracle.sap import SAP
     lat, op, _ = small
     lat.set_params(block=block, ncy=3, nmr=4, sap_half=half)
-    eta = synth.random_spinor(lat.dims, 11, nrhs=2)
+    eta = synth.random_spinor(lat.dims, 11, nrhs=nrhs)
     out = to_host(lat.apply_sap(to_dev(eta), precision=prec))
     s = SAP(op, block, ncy=3, nmr=4)
     ref = np.stack([s.apply(e) for e in eta])
-    name = "sap_%s_h%d_%s" % (prec, half, "x".join(map(str, block)))
+    name = "sap_%s_h%d_%s_n%d" % (prec, half, "x".join(map(str, block)), nrhs)
     assert record(name, elem_err(out, ref)) < tol
     assert record(name + "_faces", elem_err_faces(out, ref, lat.dims, block)) < tol
 
