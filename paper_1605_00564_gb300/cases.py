@@ -3,6 +3,7 @@ profiling one kernel at a time (a few hundred MB on the device, larger than
 L2 where DRAM figures matter).
 
     python -m paper_1605_00564_gb300.cases dslash      # FP32 Dslash, 32^3x64, 1 RHS, 3 launches
+    python -m paper_1605_00564_gb300.cases dslash12    # FP32 Dslash, 32^3x64, 12 RHS, 3 launches
     python -m paper_1605_00564_gb300.cases sap         # SAP sweeps, 16^3x32, 12 RHS, FP16 block copies
     python -m paper_1605_00564_gb300.cases sap32       # same with FP32 block copies
     python -m paper_1605_00564_gb300.cases deflation   # deflation setup + one deflated sloppy solve, 16^3x32
@@ -26,10 +27,10 @@ def _lattice(dims, eps=0.15, csw=1.9, kappa=0.136, seed=7):
     return lat
 
 
-def dslash():
+def dslash(nrhs=1):
     import torch
     lat = _lattice((64, 32, 32, 32))
-    psi = torch.randn(lat.spinor_shape(1), dtype=torch.complex128, device="cuda")
+    psi = torch.randn(lat.spinor_shape(nrhs), dtype=torch.complex128, device="cuda")
     for _ in range(3):
         lat.apply_dirac(psi, precision="f32")
 
@@ -70,7 +71,7 @@ def gcr(basis_half=1):
     lat.solve(eta, 1e-3)
 
 
-CASES = {"dslash": dslash, "sap": sap, "sap32": lambda: sap(0), "deflation": deflation, "contract": contract,
+CASES = {"dslash": dslash, "dslash12": lambda: dslash(12), "sap": sap, "sap32": lambda: sap(0), "deflation": deflation, "contract": contract,
          "gcr": gcr, "gcr32": lambda: gcr(0)}
 
 if __name__ == "__main__":

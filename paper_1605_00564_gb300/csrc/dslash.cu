@@ -6,11 +6,39 @@
 // that cover the same run of sites are adjacent in launch order, so the
 // gauge and clover words of those sites are reused from L2 across the RHS.
 // Every (1 -+ g_mu) projection halves the spinor before the SU(3) multiply.
+//
+// Traversal order with several RHS: a run of DSLASH_TPB sites is part of one
+// (t, z) plane; runs are visited slab by slab, a slab being zw consecutive z
+// planes, and within a slab time-slice by time-slice.  A site's neighbours in
+// t are then zw planes (zw X Y sites) away in launch order instead of a whole
+// time-slice: with 12 RHS a time-slice of 32^3 sites moves ~75 MB, more than
+// L2 keeps, while a slab of 8 planes moves ~20 MB, so the t-neighbours'
+// spinors are still in L2 when they are read.
 #include "qcd_internal.cuh"
 
 namespace {
 
 constexpr int DSLASH_TPB = 128;
+
+// cp: runs of DSLASH_TPB sites per (t, z) plane (0: plain lexicographic
+// order); zw: z planes per slab
+struct RunOrder {
+  int cp, zw;
+};
+
+// first site of run q
+__device__ inline int run_base(const Geom& g, RunOrder o, int q) {
+  if (o.cp == 0) return q * DSLASH_TPB;
+  const int per_t = o.zw * o.cp;
+  const int per_slab = g.L[0] * per_t;
+  const int zb = q / per_slab;
+  int r = q - zb * per_slab;
+  const int t = r / per_t;
+  r -= t * per_t;
+  const int z = zb * o.zw + r / o.cp;
+  const int run = r % o.cp;
+  return (t * g.L[3] + z) * g.L[2] * g.L[1] + run * DSLASH_TPB;
+}
 
 template <typename F, int MU, int DAGGER>
 __device__ inline void hop_dir(Spinor<typename F::R>& acc, const void* in, const void* gauge, const Geom& g, int s,
@@ -41,10 +69,11 @@ __device__ inline void hop_dir(Spinor<typename F::R>& acc, const void* in, const
 template <typename F, typename O, int DAGGER>
 __global__ void __launch_bounds__(DSLASH_TPB) k_dslash(const char* __restrict__ in, char* __restrict__ out,
                                                        const void* __restrict__ gauge, const void* __restrict__ clover,
-                                                       Geom g, typename F::R kappa, int nrhs, const int* mask) {
+                                                       Geom g, typename F::R kappa, int nrhs, const int* mask,
+                                                       RunOrder ord) {
   using R = typename F::R;
   const int rhs = blockIdx.x % nrhs;
-  const int s = (blockIdx.x / nrhs) * DSLASH_TPB + threadIdx.x;
+  const int s = run_base(g, ord, blockIdx.x / nrhs) + threadIdx.x;
   if (s >= g.V) return;
   if (mask && !mask[rhs]) return;
   const size_t off = (size_t)rhs * F::spinor_bytes * g.V;
@@ -65,12 +94,19 @@ qcd_status launch(qcd_ctx* c, const void* in, void* out, const void* gauge, cons
                   const int* mask) {
   int nb = (c->g.V + DSLASH_TPB - 1) / DSLASH_TPB;
   dim3 grid((unsigned)nb * nrhs);
+  // slab order with several RHS when a (t, z) plane holds whole runs
+  RunOrder ord = {0, 1};
+  const int plane = c->g.L[1] * c->g.L[2];
+  if (nrhs > 1 && plane % DSLASH_TPB == 0) {
+    ord.cp = plane / DSLASH_TPB;
+    ord.zw = c->g.L[3] % 8 == 0 ? 8 : c->g.L[3] % 4 == 0 ? 4 : c->g.L[3] % 2 == 0 ? 2 : 1;
+  }
   if (dagger)
     k_dslash<F, O, 1><<<grid, DSLASH_TPB, 0, c->stream>>>((const char*)in, (char*)out, gauge, clover, c->g,
-                                                          (typename F::R)c->kappa, nrhs, mask);
+                                                          (typename F::R)c->kappa, nrhs, mask, ord);
   else
     k_dslash<F, O, 0><<<grid, DSLASH_TPB, 0, c->stream>>>((const char*)in, (char*)out, gauge, clover, c->g,
-                                                          (typename F::R)c->kappa, nrhs, mask);
+                                                          (typename F::R)c->kappa, nrhs, mask, ord);
   QCD_CUDA_OK(cudaGetLastError());
   return QCD_OK;
 }

@@ -27,14 +27,16 @@ def big():
 
 
 def test_dirac_fullsize(big):
+    """One RHS (lexicographic runs) and two RHS (z-slab traversal order)."""
     lat, op = big
-    psi = synth.random_spinor(lat.dims, 81)
-    ref = op.D(psi)
+    psi = synth.random_spinor(lat.dims, 81, nrhs=2)
+    ref = np.stack([op.D(p) for p in psi])
     edge = [0, lat.T - 1]
     for prec, tol in (("f64", 1e-13), ("f32", 5e-6)):
-        out = to_host(lat.apply_dirac(to_dev(psi[None]), precision=prec))[0]
-        assert record("dirac_fullsize_" + prec, elem_err(out, ref)) < tol
-        assert elem_err(out[edge, :], ref[edge, :]) < tol
+        for n in (1, 2):
+            out = to_host(lat.apply_dirac(to_dev(psi[:n]), precision=prec))
+            assert record("dirac_fullsize_%s_n%d" % (prec, n), elem_err(out, ref[:n])) < tol
+            assert elem_err(out[:, edge], ref[:n, edge]) < tol
 
 
 @pytest.mark.parametrize("tol,basis_half", [(1e-10, 0), (1e-3, 0), (1e-3, 1)])

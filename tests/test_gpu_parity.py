@@ -35,12 +35,18 @@ def small():
 
 
 @pytest.fixture(scope="module")
+def slabbed():
+    # X Y = 256: several RHS are traversed in z-slabs of (t, z)-plane runs
+    return make_lattice((8, 16, 16, 8), eps=0.3, csw=1.4, kappa=0.126, seed=78)
+
+
+@pytest.fixture(scope="module")
 def ragged():
     # extents that are not multiples of the CTA size in any direction
     return make_lattice((6, 6, 10, 2), eps=0.4, csw=1.7, kappa=0.128, seed=77)
 
 
-@pytest.mark.parametrize("which", ["small", "ragged"])
+@pytest.mark.parametrize("which", ["small", "ragged", "slabbed"])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_dirac_fp64(request, which, dagger):
     lat, op, _ = request.getfixturevalue(which)
@@ -53,7 +59,7 @@ def test_dirac_fp64(request, which, dagger):
     assert elem_err(out[:, edge], ref[:, edge]) < 1e-13
 
 
-@pytest.mark.parametrize("which", ["small", "ragged"])
+@pytest.mark.parametrize("which", ["small", "ragged", "slabbed"])
 def test_dirac_fp32(request, which):
     lat, op, _ = request.getfixturevalue(which)
     psi = synth.random_spinor(lat.dims, 4, nrhs=2)
