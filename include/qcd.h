@@ -207,6 +207,32 @@ qcd_status qcd_nucleon_2pt(qcd_ctx* ctx, const double* prop, const int src[4], d
 qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_exact, double sloppy_tol,
                                double exact_tol, double* corr_ama, double* corr_all, qcd_rhs_stats* stats);
 
+/* Nucleon three-point functions with the isovector insertions of the
+ * axial, scalar and tensor charges (Sec. 2.3, eqs. R_A, R_S, R_T):
+ *   C3_O(t) = sum_{x at t_s, y at t} tr[P <N(x) O(y) N-bar(src)>],
+ *   O = u-bar Gamma u - d-bar Gamma d (connected insertions, u = d),
+ * for O = A_3 (Gamma = g3 g5, P = P53 = P g5 g3), S (Gamma = 1, P) and T_12
+ * (Gamma = sigma_12, P53), with P = P+ = (1 + g0)/2 for direction = +1
+ * (sink at src_t + t_sep) and P = P- = (1 - g0)/2 for direction = -1 (sink at
+ * src_t - t_sep, the backward-propagating nucleon), times modulo T.
+ * Method: sequential propagators through the sink (12 solves per projector,
+ * 24 in all, to the relative tolerance tol with the context's solver).
+ *   prop   device, canonical FP64: the 12 spinors of the point source at src
+ *          (rhs = 3 spin + colour), solutions of D psi = eta as qcd_solve
+ *          returns them (kappa normalisation).
+ *   t_sep  source-sink separation, 1 <= t_sep < T.
+ *   corr3  host [3][T][2]: insertion (A_3, S, T_12), operator time relative to
+ *          the source, re/im.  Times and the boundary sign follow
+ *          qcd_nucleon_2pt: a sink earlier than the source in absolute time is
+ *          multiplied by time_bc^3, so C3 / C2 pairs values of one convention;
+ *          the ratios of Wilson-normalised propagators are
+ *          R = 2 kappa C3(t) / C2(t_sep), C2 from qcd_nucleon_2pt (P+ or P-).
+ *   stats  host, 24 entries (sequential solves: P, then P53) or NULL.
+ * Returns QCD_ERR_NOT_CONVERGED if a sequential solve did not converge (corr3
+ * is still written). */
+qcd_status qcd_nucleon_3pt(qcd_ctx* ctx, const double* prop, const int src[4], int t_sep, int direction, double tol,
+                           double* corr3, qcd_rhs_stats* stats);
+
 /* The site-diagonal part A(x) = 1 + i kappa c_sw sum sigma F of the operator
  * (the O(a)-improvement (clover) term of Sec. 2.2's Wilson-clover operator)
  * as [site][chirality 2][6][6] complex FP64 (device), chirality block 0 acting

@@ -13,168 +13,16 @@
 //   normalisation: S = D_w^-1 = 2 kappa D^-1 with D the kappa-normalised
 //   operator of the library.
 //
-// Gamma structure (chiral basis): G = C g5 = diag(J, J), J = [[0,-1],[1,0]],
-// G' = g0 G^+ g0^T = -G; both act as "flip the index by ^1 and multiply by
-// g(i) g(j)", g(b) = -1 for even b, +1 for odd b.  P+- = (1 +- g0)/2 with
-// g0_{i, i^2} = -1.  The two parities enter through one weighted projector
+// P+- = (1 +- g0)/2 with g0_{i, i^2} = -1 in the chiral basis.  The two
+// parities enter through one weighted projector per time-slice,
 // Pw = conj(g+) P+ + conj(g-) P- = (1/2) [ws 1 - wd X], ws = conj(g+) + conj(g-),
-// wd = conj(g+) - conj(g-), X_{i, i^2} = 1.
+// wd = conj(g+) - conj(g-), X_{i, i^2} = 1, whose derivative kernel
+// (nucleon_grad.cuh) gives H_f = sum_{p,t} g(p,t) conj(dC(p,t)/dS_f).
 #include <vector>
 
-#include "qcd_internal.cuh"
+#include "nucleon_grad.cuh"
 
 namespace {
-
-__constant__ int c_perm_fh[6][4] = {  // a, b, c, sign
-    {0, 1, 2, 1}, {1, 2, 0, 1}, {2, 0, 1, 1}, {0, 2, 1, -1}, {2, 1, 0, -1}, {1, 0, 2, -1}};
-
-using C64 = Cplx<double>;
-
-__device__ inline double gs(int b) { return (b & 1) ? 1.0 : -1.0; }
-
-struct M4 {
-  C64 m[4][4];
-};
-
-__device__ inline M4 load_blk(const C64* S_s, int ns, int i, int x, int xp) {
-  M4 o;
-#pragma unroll
-  for (int al = 0; al < 4; al++)
-#pragma unroll
-    for (int alp = 0; alp < 4; alp++) o.m[al][alp] = S_s[((3 * al + x) * 12 + 3 * alp + xp) * ns + i];
-  return o;
-}
-__device__ inline M4 mm(const M4& a, const M4& b) {
-  M4 o;
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      C64 s = cmk(0.0, 0.0);
-#pragma unroll
-      for (int k = 0; k < 4; k++) s = s + a.m[i][k] * b.m[k][j];
-      o.m[i][j] = s;
-    }
-  return o;
-}
-// (G X G')-type sandwich: out_{ij} = g(i) g(j) X_{i^1, j^1}
-__device__ inline M4 flip(const M4& X) {
-  M4 o;
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) o.m[i][j] = (gs(i) * gs(j)) * X.m[i ^ 1][j ^ 1];
-  return o;
-}
-// M = G'^T X^T G^T: M_{ij} = g(i) g(j) X_{j^1, i^1}
-__device__ inline M4 flipT(const M4& X) {
-  M4 o;
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) o.m[i][j] = (gs(i) * gs(j)) * X.m[j ^ 1][i ^ 1];
-  return o;
-}
-// Pw as a matrix
-__device__ inline M4 pw_matrix(C64 ws, C64 wd) {
-  M4 o;
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      C64 v = cmk(0.0, 0.0);
-      if (i == j) v = 0.5 * ws;
-      if (j == (i ^ 2)) v = v - 0.5 * wd;
-      o.m[i][j] = v;
-    }
-  return o;
-}
-__device__ inline C64 trace_prod(const M4& a, const M4& b) {   // tr[a b]
-  C64 s = cmk(0.0, 0.0);
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int k = 0; k < 4; k++) s = s + a.m[i][k] * b.m[k][i];
-  return s;
-}
-
-// H_f for NS sites per CTA; thread = (site i, output o), o = 9 f + 3 x + x'
-// holding the 4x4 spin block (x, x') of flavour f (0: u, 1: d).
-// gw[t] = (ws, wd) for timeslice t.  prop: internal FP64 layout, 12 fields;
-// H: internal FP64 layout, 24 fields (u then d), rhs = 3 alpha' + x'.
-__global__ void k_nucleon_bwd(const double2* __restrict__ prop, const double2* __restrict__ gw, int V, int L3, int ns,
-                              double2* __restrict__ H) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C64* S_s = (C64*)smem_raw;
-  const int s0 = blockIdx.x * ns;
-  for (int idx = threadIdx.x; idx < 144 * ns; idx += blockDim.x) {
-    int i = idx % ns, e = idx / ns;
-    int comp = e / 12, rhs = e - comp * 12;
-    double2 v = prop[((size_t)rhs * 12 + comp) * V + s0 + i];
-    S_s[e * ns + i] = cmk(v.x, v.y);
-  }
-  __syncthreads();
-  const int i = threadIdx.x % ns, o = threadIdx.x / ns;
-  if (o >= 18) return;
-  const int f = o / 9, x = (o % 9) / 3, xp = o % 3;
-  const int t = (s0 + i) / L3;
-  const double2 w0 = gw[2 * t], w1 = gw[2 * t + 1];
-  const M4 Pw = pw_matrix(cmk(w0.x, w0.y), cmk(w1.x, w1.y));
-  M4 acc;
-#pragma unroll
-  for (int a = 0; a < 4; a++)
-#pragma unroll
-    for (int b = 0; b < 4; b++) acc.m[a][b] = cmk(0.0, 0.0);
-  for (int p = 0; p < 6; p++) {
-    const int a = c_perm_fh[p][0], b = c_perm_fh[p][1], c = c_perm_fh[p][2];
-    for (int q = 0; q < 6; q++) {
-      const int ap = c_perm_fh[q][0], bp = c_perm_fh[q][1], cp = c_perm_fh[q][2];
-      const double ee = (double)(c_perm_fh[p][3] * c_perm_fh[q][3]);
-      // first Wick term: ee tr[Pw S^{cc'}] tr[S^{aa'T} G S^{bb'} G']
-      if (f == 0 && x == a && xp == ap) {          // d/dS_u^{aa'} = ee trP(S^{cc'}) (G S^{bb'} G')
-        C64 tp = trace_prod(Pw, load_blk(S_s, ns, i, c, cp));
-        M4 Y = flip(load_blk(S_s, ns, i, b, bp));
-        for (int u = 0; u < 4; u++)
-          for (int v = 0; v < 4; v++) acc.m[u][v] = acc.m[u][v] + (ee * tp) * Y.m[u][v];
-      }
-      if (f == 0 && x == c && xp == cp) {          // d/dS_u^{cc'}_{al al'} = ee Pw_{al' al} T
-        M4 A = load_blk(S_s, ns, i, a, ap), B = flip(load_blk(S_s, ns, i, b, bp));
-        C64 T = cmk(0.0, 0.0);
-        for (int u = 0; u < 4; u++)
-          for (int v = 0; v < 4; v++) T = T + A.m[u][v] * B.m[u][v];
-        for (int u = 0; u < 4; u++)
-          for (int v = 0; v < 4; v++) acc.m[u][v] = acc.m[u][v] + (ee * T) * Pw.m[v][u];
-      }
-      if (f == 1 && x == b && xp == bp) {          // d/dS_d^{bb'} = ee trP(S^{cc'}) (G^T S^{aa'} G'^T)
-        C64 tp = trace_prod(Pw, load_blk(S_s, ns, i, c, cp));
-        M4 Y = flip(load_blk(S_s, ns, i, a, ap));
-        for (int u = 0; u < 4; u++)
-          for (int v = 0; v < 4; v++) acc.m[u][v] = acc.m[u][v] + (ee * tp) * Y.m[u][v];
-      }
-      // second Wick term (subtracted): ee tr[Pw S^{ca'} M S^{ac'}], M = G'^T S^{bb'T} G^T
-      if (f == 0 && x == c && xp == ap) {          // d/dS_u^{ca'}_{jk} = ee (M S^{ac'} Pw)_{kj}
-        M4 Z = mm(mm(flipT(load_blk(S_s, ns, i, b, bp)), load_blk(S_s, ns, i, a, cp)), Pw);
-        for (int u = 0; u < 4; u++)
-          for (int v = 0; v < 4; v++) acc.m[u][v] = acc.m[u][v] - ee * Z.m[v][u];
-      }
-      if (f == 0 && x == a && xp == cp) {          // d/dS_u^{ac'}_{jk} = ee (Pw S^{ca'} M)_{kj}
-        M4 Z = mm(mm(Pw, load_blk(S_s, ns, i, c, ap)), flipT(load_blk(S_s, ns, i, b, bp)));
-        for (int u = 0; u < 4; u++)
-          for (int v = 0; v < 4; v++) acc.m[u][v] = acc.m[u][v] - ee * Z.m[v][u];
-      }
-      if (f == 1 && x == b && xp == bp) {          // d/dS_d^{bb'}_{nm} = ee (G^T (S^{ac'} Pw S^{ca'}) G'^T)_{nm}
-        M4 Z = flip(mm(mm(load_blk(S_s, ns, i, a, cp), Pw), load_blk(S_s, ns, i, c, ap)));
-        for (int u = 0; u < 4; u++)
-          for (int v = 0; v < 4; v++) acc.m[u][v] = acc.m[u][v] - ee * Z.m[u][v];
-      }
-    }
-  }
-  // acc = sum_p conj(g_p) dC_p/dS; H = conj(acc).  Entry (al, al') -> field rhs = 3 al' + x', comp 3 al + x
-  double2* Hf = H + (size_t)f * 12 * 12 * V;
-  for (int al = 0; al < 4; al++)
-    for (int alp = 0; alp < 4; alp++)
-      Hf[((size_t)(3 * alp + xp) * 12 + 3 * al + x) * V + s0 + i] = make_double2(acc.m[al][alp].re, -acc.m[al][alp].im);
-}
 
 // out = scale G in for G = g5 (which 0), g3 g5 (which 1) or 1 (which 2), internal FP64 layout
 __global__ void k_gamma(const double2* __restrict__ in, double2* __restrict__ out, int which, double scale, int V,
@@ -296,28 +144,36 @@ extern "C" qcd_status qcd_fh_gradient(qcd_ctx* c, const double* prop, const int 
   QCD_TRY(devbuf_ensure(c->wsD[0], f64 * 24));
   QCD_TRY(devbuf_ensure(c->wsD[1], f64 * 24));
   QCD_TRY(layout_spinor_import(c, prop, c->wsD[4].p, QCD_PREC_F64, 12));
-  // weights per timeslice: C_out[p][trel] = sign(t) c_p(t)
-  std::vector<double2> gw(2 * T);
+  // weighted projector per timeslice: C_out[p][trel] = sign(t) c_p(t)
+  std::vector<double2> pm(16 * (size_t)T);
   const int bc3 = c->g.bc_t * c->g.bc_t * c->g.bc_t;
   for (int t = 0; t < T; t++) {
     int trel = (t - src[0] + T) % T;
     double sg = t < src[0] ? (double)bc3 : 1.0;
     double2 gp = make_double2(sg * gcorr[2 * trel], sg * gcorr[2 * trel + 1]);
     double2 gm = make_double2(sg * gcorr[2 * (T + trel)], sg * gcorr[2 * (T + trel) + 1]);
-    // conj(g+) + conj(g-), conj(g+) - conj(g-)
-    gw[2 * t] = make_double2(gp.x + gm.x, -(gp.y + gm.y));
-    gw[2 * t + 1] = make_double2(gp.x - gm.x, -(gp.y - gm.y));
+    // ws = conj(g+) + conj(g-), wd = conj(g+) - conj(g-)
+    const double2 ws = make_double2(gp.x + gm.x, -(gp.y + gm.y));
+    const double2 wd = make_double2(gp.x - gm.x, -(gp.y - gm.y));
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++) {
+        double2 v = make_double2(0.0, 0.0);
+        if (i == j) v = make_double2(0.5 * ws.x, 0.5 * ws.y);
+        if (j == (i ^ 2)) v = make_double2(v.x - 0.5 * wd.x, v.y - 0.5 * wd.y);
+        pm[16 * (size_t)t + 4 * i + j] = v;
+      }
   }
-  QCD_TRY(devbuf_ensure(c->contract, sizeof(double2) * 2 * T));
-  QCD_CUDA_OK(cudaMemcpyAsync(c->contract.p, gw.data(), sizeof(double2) * 2 * T, cudaMemcpyHostToDevice, c->stream));
+  QCD_TRY(devbuf_ensure(c->contract, sizeof(double2) * 16 * T));
+  QCD_CUDA_OK(cudaMemcpyAsync(c->contract.p, pm.data(), sizeof(double2) * 16 * T, cudaMemcpyHostToDevice, c->stream));
   int ns = 8;
   while (L3 % ns) ns >>= 1;
   {
     ProfScope ps(c, FAM_CONTRACT, (double)V * (2304 + 2 * 2304), (double)V * 36 * 6 * 200 * 8);
-    const size_t smem = sizeof(C64) * 144 * ns;
-    QCD_CUDA_OK(cudaFuncSetAttribute(k_nucleon_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_nucleon_bwd<<<V / ns, 18 * ns, smem, c->stream>>>((const double2*)c->wsD[4].p, (const double2*)c->contract.p,
-                                                       V, L3, ns, (double2*)c->wsD[5].p);
+    const size_t smem = sizeof(Cplx<double>) * 144 * ns;
+    QCD_CUDA_OK(cudaFuncSetAttribute(nucleon_grad::k_dC_dS, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    nucleon_grad::k_dC_dS<<<V / ns, 18 * ns, smem, c->stream>>>((const double2*)c->wsD[4].p,
+                                                               (const double2*)c->contract.p, V, L3, ns, 0,
+                                                               (double2*)c->wsD[5].p);
     QCD_CUDA_OK(cudaGetLastError());
   }
   // adjoint solve: X = D^-1 g5 H, Y = 2 kappa g5 X

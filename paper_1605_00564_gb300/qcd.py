@@ -30,6 +30,7 @@ EXPORTS = (
     "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_get_clover", "qcd_profile_enable", "qcd_profile_read",
     "qcd_deflation_setup", "qcd_deflation_fields", "qcd_deflation_little_matrix", "qcd_deflation_little",
     "qcd_nucleon_2pt_noalloc", "qcd_autotune", "qcd_fh_forward", "qcd_fh_gradient", "qcd_solve_multi",
+    "qcd_nucleon_3pt",
 )
 
 
@@ -92,6 +93,7 @@ def load_library(path=LIB_PATH):
     L.qcd_apply_sap.argtypes = [vp, vp, vp, i, i]
     L.qcd_solve.argtypes = [vp, vp, vp, i, dp, ctypes.POINTER(RhsStats)]
     L.qcd_nucleon_2pt.argtypes = [vp, vp, ip, dp, i]
+    L.qcd_nucleon_3pt.argtypes = [vp, vp, ip, i, i, d, dp, ctypes.POINTER(RhsStats)]
     L.qcd_ama_nucleon_2pt.argtypes = [vp, ip, i, i, d, d, dp, dp, ctypes.POINTER(RhsStats)]
     L.qcd_get_clover.argtypes = [vp, vp]
     L.qcd_nucleon_2pt_noalloc.argtypes = [ip, i, vp, ip, vp, i, vp]
@@ -275,6 +277,19 @@ class Lattice:
         _check(_lib.qcd_nucleon_2pt(self._ctx, _dev_ptr(prop), (ctypes.c_int * 4)(*src),
                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), PREC[precision]))
         return out[..., 0] + 1j * out[..., 1]
+
+    def nucleon_3pt(self, prop, src, t_sep, direction=1, tol=1e-10, allow_not_converged=False):
+        """Isovector three-point functions C3[insertion (A_3, S, T_12), t] (host
+        numpy complex) from the 12-spinor point-source propagator prop, sink at
+        src_t + direction * t_sep; returns (C3, stats of the 24 sequential solves)."""
+        prop = prop.contiguous()
+        out = np.zeros((3, self.T, 2), dtype=np.float64)
+        stats = (RhsStats * 24)()
+        self._after_torch()
+        st = _lib.qcd_nucleon_3pt(self._ctx, _dev_ptr(prop), (ctypes.c_int * 4)(*src), int(t_sep), int(direction),
+                                  float(tol), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats)
+        _check(st, allow=(4,) if allow_not_converged else ())
+        return out[..., 0] + 1j * out[..., 1], [s.as_dict() for s in stats]
 
     def ama_nucleon_2pt(self, srcs, n_exact, sloppy_tol, exact_tol, allow_not_converged=False):
         """AMA nucleon two-point function; returns (ama[2,T], all[n_src+n_exact,2,T], stats)."""
