@@ -233,6 +233,62 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_ex
 qcd_status qcd_nucleon_3pt(qcd_ctx* ctx, const double* prop, const int src[4], int t_sep, int direction, double tol,
                            double* corr3, qcd_rhs_stats* stats);
 
+/* All-mode averaging of the nucleon two- and three-point functions
+ * (Sec. 2.1, eqs. caa1, caa2), with the sloppy solves either to a relative
+ * tolerance or, as in the paper's production runs (Sec. 3, Table 3), with a
+ * fixed number N_iter of GCR iterations, separately for the point-source
+ * propagators (2pt) and the sequential propagators (3pt).
+ *   n_exact     N_org: the first n_exact source positions are also solved to
+ *               exact_tol (the bias correction); their point-source solves
+ *               start from the sloppy solutions.
+ *   sloppy_tol, exact_tol   relative tolerances in (0, 1); sloppy_tol is used
+ *               where the corresponding n_iter is 0.
+ *   n_iter_2pt  > 0: every sloppy point-source solve runs exactly this many
+ *               GCR iterations (no tolerance; not an error).
+ *   n_iter_3pt  > 0: every sloppy sequential solve likewise.
+ *   t_sep       0: two-point functions only; 1 <= t_sep < T: also the
+ *               three-point functions of qcd_nucleon_3pt with this separation.
+ *   direction   +1 / -1: sink at src_t +- t_sep (P+ / P-), as qcd_nucleon_3pt. */
+typedef struct {
+  int n_exact;
+  double sloppy_tol;
+  double exact_tol;
+  int n_iter_2pt;
+  int n_iter_3pt;
+  int t_sep;
+  int direction;
+} qcd_ama_params;
+
+/* src: host [n_src][4] source positions (multiples of the SAP block extents,
+ * differing from src[0] by an even number of blocks, as qcd_ama_nucleon_2pt).
+ *   c2_ama  host [2][T][2]          AMA estimate of the two-point function
+ *                                   (P+, P-; layout of qcd_nucleon_2pt)
+ *   c3_ama  host [3][T][2] or NULL  AMA estimate of the three-point functions
+ *                                   (needed when t_sep > 0; layout of qcd_nucleon_3pt)
+ *   c2_all  host [n_src + n_exact][2][T][2] or NULL: sloppy correlators of
+ *           every position, then exact ones of the first n_exact
+ *   c3_all  host [n_src + n_exact][3][T][2] or NULL, same order
+ *   stats   host [n_src + n_exact][12 (+ 24 with t_sep)] or NULL: point-source
+ *           solves, then the sequential solves of each position
+ * Work is stream-ordered on the context's stream; the call returns after the
+ * correlators are on the host.  Returns the first non-OK status of a solve
+ * (a fixed-iteration solve that stops at N_iter counts as OK). */
+qcd_status qcd_ama_nucleon(qcd_ctx* ctx, const int* src, int n_src, const qcd_ama_params* p, double* c2_ama,
+                           double* c3_ama, double* c2_all, double* c3_all, qcd_rhs_stats* stats);
+
+/* The error model of the AMA estimator (eqs. ama1-ama3; host computation,
+ * no device work) from measurements of one observable on n_conf gauge
+ * configurations: exact [n_conf][n_org] (O^f), appx_org [n_conf][n_org]
+ * (O_appx^f at the same positions), appx [n_conf][n_g] (O_appx^g).  With
+ * sample covariances over the configurations,
+ *   out[0] = Delta r = (1/N_org - 1/N_G) (1 - (1/N_org) sum_f corr(O^f, O_appx^f))
+ *   out[1] = R = (1/N_G^2) sum_{g != g'} corr(O_appx^g, O_appx^g')
+ *   out[2] = sqrt(1/N_G + 2 Delta r + R), the model of sigma_AMA / sigma
+ *   out[3] = the measured std(O_AMA) / sqrt(mean_f var(O^f)).
+ * QCD_ERR_ARG if n_conf < 2, n_org > n_g or a measurement has zero variance. */
+qcd_status qcd_ama_error_model(const double* exact, const double* appx_org, const double* appx, int n_conf,
+                               int n_org, int n_g, double* out);
+
 /* The site-diagonal part A(x) = 1 + i kappa c_sw sum sigma F of the operator
  * (the O(a)-improvement (clover) term of Sec. 2.2's Wilson-clover operator)
  * as [site][chirality 2][6][6] complex FP64 (device), chirality block 0 acting

@@ -205,45 +205,24 @@ __global__ void k_three_pt_final(const double2* __restrict__ part, int per_t, in
 
 }  // namespace
 
-extern "C" qcd_status qcd_nucleon_3pt(qcd_ctx* c, const double* prop, const int src[4], int t_sep, int direction,
-                                      double tol, double* corr3, qcd_rhs_stats* stats) {
-  if (!c || !prop || !src || !corr3) {
-    qcd_set_error("null argument");
-    return QCD_ERR_ARG;
-  }
-  if (!c->have_gauge) {
-    qcd_set_error("no gauge field loaded");
-    return QCD_ERR_STATE;
-  }
+// Three-point functions of the point-source propagator S_int (12 FP64
+// fields in the internal layout, not in wsD[0..3] or wsD[5..7]) at src, sink
+// at src_t + direction t_sep.  Sequential solves to tol, or with n_iter > 0
+// exactly n_iter GCR iterations each (the fixed-iteration sloppy mode of
+// Sec. 3, Table 3; such solves count as successful).  corr3: host [3][T][2];
+// st: 24 entries.
+qcd_status threept_internal(qcd_ctx* c, const void* S_int, const int src[4], int t_sep, int direction, double tol,
+                            int n_iter, double* corr3, qcd_rhs_stats* st) {
   const int V = c->g.V, T = c->g.L[0], L3 = V / T;
-  for (int mu = 0; mu < 4; mu++)
-    if (src[mu] < 0 || src[mu] >= c->g.L[mu]) {
-      qcd_set_error("source outside the lattice");
-      return QCD_ERR_ARG;
-    }
-  if (t_sep < 1 || t_sep >= T) {
-    qcd_set_error("t_sep must be in [1, T)");
-    return QCD_ERR_ARG;
-  }
-  if (direction != 1 && direction != -1) {
-    qcd_set_error("direction must be +1 (forward, P+) or -1 (backward, P-)");
-    return QCD_ERR_ARG;
-  }
-  if (!(tol > 0 && tol < 1)) {
-    qcd_set_error("tol must be in (0, 1)");
-    return QCD_ERR_ARG;
-  }
   const int t0 = src[0];
   const int ts = ((t0 + direction * t_sep) % T + T) % T;
   const int bc3 = c->g.bc_t * c->g.bc_t * c->g.bc_t;
   const double sign = ts < t0 ? (double)bc3 : 1.0;   // as the two-point function's wrapped sink times
   const size_t f64 = spinor_bytes(c, QCD_PREC_F64);
-  // S (12) in wsD[4]; H (24: u, d) in wsD[5]; eta (24: P, P53) in wsD[6]; W (24) in wsD[7]
-  QCD_TRY(devbuf_ensure(c->wsD[4], f64 * 12));
+  // H (24: u, d) in wsD[5]; eta (24: P, P53) in wsD[6]; W (24) in wsD[7]
   QCD_TRY(devbuf_ensure(c->wsD[5], f64 * 24));
   QCD_TRY(devbuf_ensure(c->wsD[6], f64 * 24));
   QCD_TRY(devbuf_ensure(c->wsD[7], f64 * 24));
-  QCD_TRY(layout_spinor_import(c, prop, c->wsD[4].p, QCD_PREC_F64, 12));
   const ThreePtMats M = three_pt_mats(direction);
   int ns = 8;
   while (L3 % ns) ns >>= 1;
@@ -262,7 +241,7 @@ extern "C" qcd_status qcd_nucleon_3pt(qcd_ctx* c, const double* prop, const int 
     {
       // the sequential source lives on the sink time-slice only
       ProfScope ps(c, FAM_CONTRACT, (double)L3 * 3 * 2304, (double)L3 * 36 * 6 * 200 * 8);
-      nucleon_grad::k_dC_dS<<<L3 / ns, 18 * ns, smem, c->stream>>>((const double2*)c->wsD[4].p,
+      nucleon_grad::k_dC_dS<<<L3 / ns, 18 * ns, smem, c->stream>>>((const double2*)S_int,
                                                                   (const double2*)c->contract.p, V, L3, ns, ts * L3,
                                                                   (double2*)c->wsD[5].p);
       QCD_CUDA_OK(cudaGetLastError());
@@ -273,18 +252,32 @@ extern "C" qcd_status qcd_nucleon_3pt(qcd_ctx* c, const double* prop, const int 
     }
   }
   // the 24 sequential propagators, 12 at a time: W = D^-1 eta
-  std::vector<qcd_rhs_stats> st(24);
-  std::vector<double> tols(12, tol);
-  for (int p = 0; p < 2; p++) {
-    QCD_TRY(devbuf_ensure(c->wsD[0], f64 * 12));
-    QCD_TRY(devbuf_ensure(c->wsD[1], f64 * 12));
-    QCD_CUDA_OK(cudaMemcpyAsync(c->wsD[0].p, (char*)c->wsD[6].p + f64 * 12 * p, f64 * 12, cudaMemcpyDeviceToDevice,
-                                c->stream));
-    QCD_CUDA_OK(cudaMemsetAsync(c->wsD[1].p, 0, f64 * 12, c->stream));
-    QCD_TRY(solver_run(c, 12, tols.data(), st.data() + 12 * p));
-    QCD_CUDA_OK(cudaMemcpyAsync((char*)c->wsD[7].p + f64 * 12 * p, c->wsD[1].p, f64 * 12, cudaMemcpyDeviceToDevice,
-                                c->stream));
+  std::vector<double> tols(12, n_iter > 0 ? 1e-300 : tol);
+  const int max_outer = c->params.max_outer;
+  if (n_iter > 0) c->params.max_outer = n_iter;
+  qcd_status rc = QCD_OK;
+  for (int p = 0; p < 2 && rc == QCD_OK; p++) {
+    if ((rc = devbuf_ensure(c->wsD[0], f64 * 12)) != QCD_OK) break;
+    if ((rc = devbuf_ensure(c->wsD[1], f64 * 12)) != QCD_OK) break;
+    if (cudaMemcpyAsync(c->wsD[0].p, (char*)c->wsD[6].p + f64 * 12 * p, f64 * 12, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->wsD[1].p, 0, f64 * 12, c->stream) != cudaSuccess) {
+      qcd_set_error("sequential source set-up failed");
+      rc = QCD_ERR_CUDA;
+      break;
+    }
+    if ((rc = solver_run(c, 12, tols.data(), st + 12 * p)) != QCD_OK) break;
+    if (cudaMemcpyAsync((char*)c->wsD[7].p + f64 * 12 * p, c->wsD[1].p, f64 * 12, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess) {
+      qcd_set_error("sequential propagator copy failed");
+      rc = QCD_ERR_CUDA;
+    }
   }
+  c->params.max_outer = max_outer;
+  QCD_TRY(rc);
+  if (n_iter > 0)
+    for (int r = 0; r < 24; r++)
+      if (st[r].status == QCD_ERR_NOT_CONVERGED) st[r].status = QCD_OK;   // stopped at n_iter by design
   // contraction with the forward propagator, per time-slice
   int cs = 128;
   while (L3 % cs) cs >>= 1;
@@ -299,7 +292,7 @@ extern "C" qcd_status qcd_nucleon_3pt(qcd_ctx* c, const double* prop, const int 
   {
     ProfScope ps(c, FAM_CONTRACT, (double)V * 36 * 192, (double)V * 12 * 3 * 12 * (4 * 8 + 8));
     const int threads = cs < 32 ? 32 : cs;
-    k_three_pt<<<nb, threads, 0, c->stream>>>((const double2*)c->wsD[7].p, (const double2*)c->wsD[4].p, mats, V, cs,
+    k_three_pt<<<nb, threads, 0, c->stream>>>((const double2*)c->wsD[7].p, (const double2*)S_int, mats, V, cs,
                                               part);
     QCD_CUDA_OK(cudaGetLastError());
     k_three_pt_final<<<(3 * T + 127) / 128, 128, 0, c->stream>>>(part, per_t, T, t0, sign, cd);
@@ -307,6 +300,42 @@ extern "C" qcd_status qcd_nucleon_3pt(qcd_ctx* c, const double* prop, const int 
   }
   QCD_CUDA_OK(cudaMemcpyAsync(corr3, cd, sizeof(double2) * 3 * T, cudaMemcpyDeviceToHost, c->stream));
   QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
+  return QCD_OK;
+}
+
+extern "C" qcd_status qcd_nucleon_3pt(qcd_ctx* c, const double* prop, const int src[4], int t_sep, int direction,
+                                      double tol, double* corr3, qcd_rhs_stats* stats) {
+  if (!c || !prop || !src || !corr3) {
+    qcd_set_error("null argument");
+    return QCD_ERR_ARG;
+  }
+  if (!c->have_gauge) {
+    qcd_set_error("no gauge field loaded");
+    return QCD_ERR_STATE;
+  }
+  const int T = c->g.L[0];
+  for (int mu = 0; mu < 4; mu++)
+    if (src[mu] < 0 || src[mu] >= c->g.L[mu]) {
+      qcd_set_error("source outside the lattice");
+      return QCD_ERR_ARG;
+    }
+  if (t_sep < 1 || t_sep >= T) {
+    qcd_set_error("t_sep must be in [1, T)");
+    return QCD_ERR_ARG;
+  }
+  if (direction != 1 && direction != -1) {
+    qcd_set_error("direction must be +1 (forward, P+) or -1 (backward, P-)");
+    return QCD_ERR_ARG;
+  }
+  if (!(tol > 0 && tol < 1)) {
+    qcd_set_error("tol must be in (0, 1)");
+    return QCD_ERR_ARG;
+  }
+  const size_t f64 = spinor_bytes(c, QCD_PREC_F64);
+  QCD_TRY(devbuf_ensure(c->wsD[4], f64 * 12));
+  QCD_TRY(layout_spinor_import(c, prop, c->wsD[4].p, QCD_PREC_F64, 12));
+  std::vector<qcd_rhs_stats> st(24);
+  QCD_TRY(threept_internal(c, c->wsD[4].p, src, t_sep, direction, tol, 0, corr3, st.data()));
   qcd_status worst = QCD_OK;
   for (int r = 0; r < 24; r++) {
     if (stats) stats[r] = st[r];

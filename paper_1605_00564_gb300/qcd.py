@@ -30,7 +30,7 @@ EXPORTS = (
     "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_get_clover", "qcd_profile_enable", "qcd_profile_read",
     "qcd_deflation_setup", "qcd_deflation_fields", "qcd_deflation_little_matrix", "qcd_deflation_little",
     "qcd_nucleon_2pt_noalloc", "qcd_autotune", "qcd_fh_forward", "qcd_fh_gradient", "qcd_solve_multi",
-    "qcd_nucleon_3pt",
+    "qcd_nucleon_3pt", "qcd_ama_nucleon", "qcd_ama_error_model",
 )
 
 
@@ -48,6 +48,12 @@ class SolverParams(ctypes.Structure):
         ("dfl_little_iters", ctypes.c_int), ("dfl_gen_iters", ctypes.c_int), ("graphs", ctypes.c_int),
         ("basis_half", ctypes.c_int),
     ]
+
+
+class AmaParams(ctypes.Structure):
+    _fields_ = [("n_exact", ctypes.c_int), ("sloppy_tol", ctypes.c_double), ("exact_tol", ctypes.c_double),
+                ("n_iter_2pt", ctypes.c_int), ("n_iter_3pt", ctypes.c_int), ("t_sep", ctypes.c_int),
+                ("direction", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -94,6 +100,8 @@ def load_library(path=LIB_PATH):
     L.qcd_solve.argtypes = [vp, vp, vp, i, dp, ctypes.POINTER(RhsStats)]
     L.qcd_nucleon_2pt.argtypes = [vp, vp, ip, dp, i]
     L.qcd_nucleon_3pt.argtypes = [vp, vp, ip, i, i, d, dp, ctypes.POINTER(RhsStats)]
+    L.qcd_ama_nucleon.argtypes = [vp, ip, i, ctypes.POINTER(AmaParams), dp, dp, dp, dp, ctypes.POINTER(RhsStats)]
+    L.qcd_ama_error_model.argtypes = [dp, dp, dp, i, i, i, dp]
     L.qcd_ama_nucleon_2pt.argtypes = [vp, ip, i, i, d, d, dp, dp, ctypes.POINTER(RhsStats)]
     L.qcd_get_clover.argtypes = [vp, vp]
     L.qcd_nucleon_2pt_noalloc.argtypes = [ip, i, vp, ip, vp, i, vp]
@@ -139,6 +147,20 @@ def nucleon_2pt_noalloc(dims, prop, src, corr, precision="f64", time_bc=-1, stre
                                      (ctypes.c_int * 4)(*src), _dev_ptr(corr), PREC[precision],
                                      ctypes.c_void_p(s.cuda_stream)))
     return corr
+
+
+def ama_error_model(exact, appx_org, appx):
+    """Error model of the AMA estimator (eqs. ama1-ama3) computed by the
+    library: exact, appx_org [n_conf, n_org], appx [n_conf, n_g] (real).
+    Returns {dr, R, model, measured}."""
+    L = load_library()
+    e = np.ascontiguousarray(exact, dtype=np.float64)
+    a0 = np.ascontiguousarray(appx_org, dtype=np.float64)
+    a = np.ascontiguousarray(appx, dtype=np.float64)
+    out = np.zeros(4)
+    dpp = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(L.qcd_ama_error_model(dpp(e), dpp(a0), dpp(a), e.shape[0], e.shape[1], a.shape[1], dpp(out)))
+    return {"dr": out[0], "R": out[1], "model": out[2], "measured": out[3]}
 
 
 class Lattice:
@@ -290,6 +312,31 @@ class Lattice:
                                   float(tol), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats)
         _check(st, allow=(4,) if allow_not_converged else ())
         return out[..., 0] + 1j * out[..., 1], [s.as_dict() for s in stats]
+
+    def ama_nucleon(self, srcs, n_exact, sloppy_tol=1e-3, exact_tol=1e-10, n_iter_2pt=0, n_iter_3pt=0, t_sep=0,
+                    direction=1, allow_not_converged=False):
+        """AMA two- (and with t_sep, three-) point functions; returns a dict with
+        c2_ama [2, T], c2_all [n, 2, T], c3_ama [3, T], c3_all [n, 3, T] (complex
+        numpy; the 3pt entries only with t_sep) and stats (list per solve)."""
+        srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32).reshape(-1, 4))
+        ns = srcs.shape[0]
+        nj = ns + int(n_exact)
+        p = AmaParams(int(n_exact), float(sloppy_tol), float(exact_tol), int(n_iter_2pt), int(n_iter_3pt), int(t_sep),
+                      int(direction))
+        c2a = np.zeros((2, self.T, 2))
+        c2 = np.zeros((nj, 2, self.T, 2))
+        c3a = np.zeros((3, self.T, 2))
+        c3 = np.zeros((nj, 3, self.T, 2))
+        stats = (RhsStats * (nj * (12 + (24 if t_sep else 0))))()
+        dpp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st = _lib.qcd_ama_nucleon(self._ctx, srcs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ns, ctypes.byref(p),
+                                  dpp(c2a), dpp(c3a), dpp(c2), dpp(c3), stats)
+        _check(st, allow=(4,) if allow_not_converged else ())
+        cx = lambda a: a[..., 0] + 1j * a[..., 1]
+        out = {"c2_ama": cx(c2a), "c2_all": cx(c2), "stats": [s.as_dict() for s in stats]}
+        if t_sep:
+            out.update({"c3_ama": cx(c3a), "c3_all": cx(c3)})
+        return out
 
     def ama_nucleon_2pt(self, srcs, n_exact, sloppy_tol, exact_tol, allow_not_converged=False):
         """AMA nucleon two-point function; returns (ama[2,T], all[n_src+n_exact,2,T], stats)."""
