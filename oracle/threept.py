@@ -100,10 +100,25 @@ def site_index(dims, x):
     return ((t * Z + z) * Y + y) * X + xx
 
 
-def three_point(op, src, t_sep, direction=+1, bc_t=-1, a2a=None):
+def _smear_sink_side(Kt, A):
+    """Apply a time-slice smearing matrix Kt [3 L3, 3 L3] (site, colour) to
+    the sink index of A [L3, 12, n] (rows: site of the time-slice, spin
+    colour); spin untouched."""
+    L3, _, n = A.shape
+    B = A.reshape(L3, 4, 3, n).transpose(1, 0, 2, 3).reshape(4, 3 * L3, n)
+    B = np.einsum("ij,sjn->sin", Kt, B)
+    return B.reshape(4, L3, 3, n).transpose(1, 0, 2, 3).reshape(L3, 12, n)
+
+
+def three_point(op, src, t_sep, direction=+1, bc_t=-1, a2a=None, smear=None):
     """C3[insertion, t_rel] for the insertions of ``INSERTIONS`` (isovector
     u - d), sink at t0 + direction * t_sep.  Returns (C3 (3, T) complex,
-    the two-point function tr[P+- G] at the sink: the ratios' denominator)."""
+    the two-point function tr[P+- G] at the sink: the ratios' denominator).
+
+    smear = (K, ) with K the per-time-slice Gaussian smearing matrices of
+    ``smearing.timeslice_matrices``: smeared source and sink, i.e. every
+    source-to-sink propagator is K S K and the propagator through the
+    operator is (K S)(x, y) Gamma (S K)(y, x0)."""
     dims = op.dims
     T = dims[0]
     a2a = a2a or AllToAll(op)
@@ -112,14 +127,30 @@ def three_point(op, src, t_sep, direction=+1, bc_t=-1, a2a=None):
     ts, wraps = sink_time(T, t0, t_sep, direction)
     sign = float(bc_t) ** 3 if wraps else 1.0
     s0 = site_index(dims, src)
-    S0 = a2a.columns(s0)                                   # (12V, 12): S(y, x0)
+    if smear is None:
+        S0 = a2a.columns(s0)                               # (12V, 12): S(y, x0)
+    else:
+        # the 12 smeared point sources K delta_{x0}: on the source time-slice only
+        K = smear[0]
+        E = np.zeros((12 * a2a.V, 12), dtype=np.complex128)
+        loc = s0 - t0 * L3
+        for al in range(4):
+            for a in range(3):
+                col = K[t0][:, 3 * loc + a].reshape(L3, 3)             # (site, colour) of the time-slice
+                for z in range(L3):
+                    E[12 * (t0 * L3 + z) + 3 * al + np.arange(3), 3 * al + a] = col[z]
+        S0 = scipy.linalg.lu_solve(a2a.lu, E)              # (S K)(y, x0)
     sink_sites = np.arange(ts * L3, (ts + 1) * L3)
     Srow = a2a.rows(sink_sites)                            # (L3, 12, 12V): S(x, y)
+    S0s = S0.reshape(a2a.V, 12, 12)[sink_sites]            # (S K)(x, x0) at the sink
+    if smear is not None:
+        Srow = _smear_sink_side(smear[0][ts], Srow)        # (K S)(x, y)
+        S0s = _smear_sink_side(smear[0][ts], S0s)          # (K S K)(x, x0)
 
     def to_mat(block):                                     # (n, 12, 12) -> (n, 4, 3, 4, 3)
         return block.reshape(block.shape[0], 4, 3, 4, 3)
 
-    S_sink = to_mat(S0.reshape(a2a.V, 12, 12)[sink_sites])  # S(x, x0) at the sink sites
+    S_sink = to_mat(S0s)
     out = np.zeros((len(INSERTIONS), T), dtype=np.complex128)
     G2 = trilinear(S_sink, S_sink, S_sink).sum(axis=0)
     c2 = sign * np.trace((P_PLUS if direction > 0 else P_MINUS) @ G2)

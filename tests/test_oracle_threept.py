@@ -71,3 +71,50 @@ def test_two_point_matches_nucleon_module(setup):
         ref = nucleon.two_point(prop, src[0])
         trel = (direction * t_sep) % op.dims[0]
         assert abs(c2 - ref[0 if direction > 0 else 1, trel]) < 1e-12 * abs(c2)
+
+
+def test_smeared_source_and_sink(setup):
+    """With Gaussian smearing at source and sink the insertion sum rule holds
+    for the smeared correlators (the coupling acts between the smearings),
+    and K = 1 (kappa_G = 0) reproduces the point correlators."""
+    from oracle import smearing
+    op, a2a = setup
+    src = (1, 0, 1, 1)
+    t_sep = 2
+    Uape = smearing.ape_smear(op.U, 0.5, 2)
+    K = smearing.timeslice_matrices(Uape, 0.3, 2)
+    c3, c2 = threept.three_point(op, src, t_sep, 1, a2a=a2a, smear=(K,))
+    p3, p2 = threept.three_point(op, src, t_sep, 1, a2a=a2a)
+    assert abs(c2 - p2) > 1e-3 * abs(p2)                          # smearing changes the correlator
+    K0 = smearing.timeslice_matrices(Uape, 0.0, 2)
+    z3, z2 = threept.three_point(op, src, t_sep, 1, a2a=a2a, smear=(K0,))
+    assert np.abs(z3 - p3).max() < 1e-12 * np.abs(p3).max() and abs(z2 - p2) < 1e-12 * abs(p2)
+    # sum rule with smeared source and sink: -d/dtheta of the smeared two-point function
+    from oracle.solve import dense_matrix
+    M = dense_matrix(op)
+    V = M.shape[0] // 12
+    T = op.dims[0]
+    L3 = V // T
+    big = np.zeros((12 * V, 12 * V), dtype=complex)     # K on every time-slice, spin untouched
+    for t in range(T):
+        for al in range(4):
+            idx = 12 * (t * L3 + np.arange(L3))[:, None] + 3 * al + np.arange(3)[None, :]
+            idx = idx.reshape(-1)
+            big[np.ix_(idx, idx)] = K[t]
+    s0 = threept.site_index(op.dims, src)
+    E = np.zeros((12 * V, 12), dtype=complex)
+    E[12 * s0 + np.arange(12), np.arange(12)] = 1.0
+    ts = (src[0] + t_sep) % T
+    Gam = threept.INSERTIONS[1][1]
+    P = threept.P_PLUS
+    h = 1e-4
+
+    def c2_at(th):
+        shift = th * np.kron(np.eye(V), np.kron(Gam, np.eye(3)))
+        Su = (big @ np.linalg.solve(M + shift, big @ E)).reshape(V, 12, 12)[ts * L3:(ts + 1) * L3]
+        Sd = (big @ np.linalg.solve(M - shift, big @ E)).reshape(V, 12, 12)[ts * L3:(ts + 1) * L3]
+        shp = (L3, 4, 3, 4, 3)
+        return np.trace(P @ threept.trilinear(Su.reshape(shp), Sd.reshape(shp), Su.reshape(shp)).sum(axis=0))
+    deriv = (c2_at(h) - c2_at(-h)) / (2 * h)
+    assert abs(c3[1].sum() + deriv) < 1e-6 * abs(deriv)
+    assert abs(c2 - c2_at(0.0)) < 1e-12 * abs(c2)
