@@ -217,6 +217,7 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* ctx, const int* src, int n_src, int n_ex
  * src_t - t_sep, the backward-propagating nucleon), times modulo T.
  * Method: sequential propagators through the sink (12 solves per projector,
  * 24 in all, to the relative tolerance tol with the context's solver).
+ * Point sink (smeared sinks: qcd_ama_nucleon with qcd_set_smearing).
  *   prop   device, canonical FP64: the 12 spinors of the point source at src
  *          (rhs = 3 spin + colour), solutions of D psi = eta as qcd_solve
  *          returns them (kappa normalisation).
@@ -288,6 +289,28 @@ qcd_status qcd_ama_nucleon(qcd_ctx* ctx, const int* src, int n_src, const qcd_am
  * QCD_ERR_ARG if n_conf < 2, n_org > n_g or a measurement has zero variance. */
 qcd_status qcd_ama_error_model(const double* exact, const double* appx_org, const double* appx, int n_conf,
                                int n_org, int n_g, double* out);
+
+/* Smeared sources and sinks (Sec. 2.3: Gaussian smearing at source and sink
+ * with APE-smeared links in the Laplacian; the paper takes the parameters
+ * from earlier work, so they are the caller's).
+ * qcd_smear_links: APE-smeared spatial links from the loaded gauge field,
+ *   n_ape steps of U'_k(x) = Proj_SU(3)[U_k(x) + alpha sum_{j != k spatial}
+ *   (U_j(x) U_k(x+j) U_j(x+k)^+ + U_j(x-j)^+ U_k(x-j) U_j(x-j+k))], Proj_SU(3)
+ *   the unitary polar factor divided by the principal cube root of its
+ *   determinant; time links unchanged.  Kept in the context (FP64); loading a
+ *   new gauge field does not update them.  alpha >= 0, 0 <= n_ape <= 1000.
+ * qcd_set_smearing: Gaussian kernel K = [(1 + kappa_g H) / (1 + 6 kappa_g)]^n_gauss,
+ *   H the spatial hopping term on the smeared links (spin untouched,
+ *   periodic in space); qcd_ama_nucleon then smears its point sources and
+ *   the sink index of its propagators (n_gauss = 0: point source and sink).
+ *   Needs qcd_smear_links first when n_gauss > 0.
+ * qcd_smear_gaussian: out = K in for nrhs device canonical spinors.
+ * qcd_get_smeared_links: the smeared links as a device canonical FP64 gauge
+ *   field [site][mu][3][3]. */
+qcd_status qcd_smear_links(qcd_ctx* ctx, double alpha, int n_ape);
+qcd_status qcd_set_smearing(qcd_ctx* ctx, double kappa_g, int n_gauss);
+qcd_status qcd_smear_gaussian(qcd_ctx* ctx, const double* in, double* out, int nrhs);
+qcd_status qcd_get_smeared_links(qcd_ctx* ctx, double* out);
 
 /* The site-diagonal part A(x) = 1 + i kappa c_sw sum sigma F of the operator
  * (the O(a)-improvement (clover) term of Sec. 2.2's Wilson-clover operator)

@@ -9,7 +9,11 @@
 // sloppily too (their own N_iter) and the three-point functions contracted;
 // the first N_org positions are then solved to the exact tolerance (the
 // point-source solve starting from its sloppy solution) and contracted
-// again.  The AMA estimate O_AMA = (1/N_org) sum_f [O^f - O_appx^f]
+// again.  With Gaussian smearing set on the context (qcd_set_smearing) the
+// point sources are smeared before the solves and the propagators' sink
+// index after them (Sec. 2.3); the three-point functions then use the
+// sink-smeared propagator for the sequential source and smear that source.
+// The AMA estimate O_AMA = (1/N_org) sum_f [O^f - O_appx^f]
 // + (1/N_G) sum_g O_appx^g is formed from the returned correlators.
 #include <math.h>
 #include <string.h>
@@ -21,8 +25,8 @@
 qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st);
 qcd_status contract_nucleon(qcd_ctx* c, const void* prop, int t0, double* corr_dev, int precision,
                             double2* partials);
-qcd_status threept_internal(qcd_ctx* c, const void* S_int, const int src[4], int t_sep, int direction, double tol,
-                            int n_iter, double* corr3, qcd_rhs_stats* st);
+qcd_status threept_internal(qcd_ctx* c, const void* S_int, const void* S_sink, const int src[4], int t_sep,
+                            int direction, double tol, int n_iter, double* corr3, qcd_rhs_stats* st);
 
 namespace {
 
@@ -106,6 +110,7 @@ extern "C" qcd_status qcd_ama_nucleon(qcd_ctx* c, const int* src, int n_src, con
       rc = QCD_ERR_CUDA;
       break;
     }
+    if ((rc = smear_fields(c, c->wsD[0].p, 12)) != QCD_OK) break;      // smeared source
     const bool fixed = !exact && p->n_iter_2pt > 0;
     std::vector<double> tols(12, exact ? p->exact_tol : (fixed ? 1e-300 : p->sloppy_tol));
     if (exact) c->params.basis_half = 0;      // an FP16 Krylov basis serves the sloppy solves only
@@ -126,12 +131,25 @@ extern "C" qcd_status qcd_ama_nucleon(qcd_ctx* c, const int* src, int n_src, con
       rc = QCD_ERR_CUDA;
       break;
     }
+    // the propagator seen at the sink: K S with a smeared sink
+    const void* S_sink = c->wsD[4].p;
+    if (c->smear_n > 0) {
+      if ((rc = devbuf_ensure(c->smearbuf[1], prop_bytes)) != QCD_OK) break;
+      if (cudaMemcpyAsync(c->smearbuf[1].p, c->wsD[4].p, prop_bytes, cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess) {
+        qcd_set_error("propagator copy failed");
+        rc = QCD_ERR_CUDA;
+        break;
+      }
+      if ((rc = smear_fields(c, c->smearbuf[1].p, 12)) != QCD_OK) break;
+      S_sink = c->smearbuf[1].p;
+    }
     // two-point function
     if ((rc = devbuf_ensure(c->contract, sizeof(double2) * (npart + 2 * T))) != QCD_OK) break;
     double2* part = (double2*)c->contract.p;
     double2* cd = part + npart;
     const int prec = exact ? QCD_PREC_F64 : c->params.precision;
-    if ((rc = contract_nucleon(c, c->wsD[4].p, s[0], (double*)cd, prec, part)) != QCD_OK) break;
+    if ((rc = contract_nucleon(c, S_sink, s[0], (double*)cd, prec, part)) != QCD_OK) break;
     if (cudaMemcpyAsync(c2.data() + (size_t)j * 4 * T, cd, sizeof(double2) * 2 * T, cudaMemcpyDeviceToHost,
                         c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -142,8 +160,9 @@ extern "C" qcd_status qcd_ama_nucleon(qcd_ctx* c, const int* src, int n_src, con
     // three-point functions
     if (p->t_sep) {
       if (exact) c->params.basis_half = 0;
-      rc = threept_internal(c, c->wsD[4].p, s, p->t_sep, p->direction, exact ? p->exact_tol : p->sloppy_tol,
-                            exact ? 0 : p->n_iter_3pt, c3.data() + (size_t)j * 6 * T, sj + 12);
+      rc = threept_internal(c, c->wsD[4].p, S_sink, s, p->t_sep, p->direction,
+                            exact ? p->exact_tol : p->sloppy_tol, exact ? 0 : p->n_iter_3pt,
+                            c3.data() + (size_t)j * 6 * T, sj + 12);
       c->params.basis_half = basis_half;
       if (rc != QCD_OK) break;
     }

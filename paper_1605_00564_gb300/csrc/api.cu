@@ -216,6 +216,9 @@ void qcd_destroy(qcd_ctx* c) {
   devbuf_free(c->contract);
   devbuf_free(c->stage);
   devbuf_free(c->guess);
+  devbuf_free(c->gaugeS);
+  devbuf_free(c->smearbuf[0]);
+  devbuf_free(c->smearbuf[1]);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   dfl_free(c);
   for (auto& gph : c->sap_graphs) cudaGraphExecDestroy(gph.exec);

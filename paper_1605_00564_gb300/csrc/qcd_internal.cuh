@@ -456,6 +456,13 @@ struct qcd_ctx {
   double* host_scal = nullptr;   // pinned mirror of scalars
   size_t host_scal_bytes = 0;
   void* dfl = nullptr;           // deflation state (dfl.cu)
+  // smeared sources and sinks (smear.cu): APE-smeared links (FP64, internal
+  // gauge layout; time links copied), Gaussian kernel parameters, scratch
+  DevBuf gaugeS;
+  int have_smeared_links = 0;
+  double smear_kappa = 0;
+  int smear_n = 0;               // 0: point sources and sinks
+  DevBuf smearbuf[2];
 };
 
 // Brackets the launches issued in its scope with CUDA events when profiling
@@ -522,3 +529,7 @@ void* dfl_phi(qcd_ctx* c);
 void* dfl_little(qcd_ctx* c);
 
 size_t spinor_bytes(const qcd_ctx* c, int prec);
+
+// Gaussian smearing (smear.cu) of nrhs FP64 internal spinors in place with
+// the context's smeared links and parameters (a no-op when smear_n is 0)
+qcd_status smear_fields(qcd_ctx* c, void* fields, int nrhs);

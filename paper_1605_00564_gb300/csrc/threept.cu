@@ -205,14 +205,17 @@ __global__ void k_three_pt_final(const double2* __restrict__ part, int per_t, in
 
 }  // namespace
 
-// Three-point functions of the point-source propagator S_int (12 FP64
-// fields in the internal layout, not in wsD[0..3] or wsD[5..7]) at src, sink
-// at src_t + direction t_sep.  Sequential solves to tol, or with n_iter > 0
+// Three-point functions of the propagator S_int from the source at src (12
+// FP64 fields in the internal layout, not in wsD[0..3] or wsD[5..7]), sink
+// at src_t + direction t_sep.  S_sink is the same propagator as seen at the
+// sink (S_int itself for a point sink; K S_int with the Gaussian kernel K of
+// a smeared sink, in which case the sequential source is smeared with K as
+// well, K being Hermitian).  Sequential solves to tol, or with n_iter > 0
 // exactly n_iter GCR iterations each (the fixed-iteration sloppy mode of
 // Sec. 3, Table 3; such solves count as successful).  corr3: host [3][T][2];
 // st: 24 entries.
-qcd_status threept_internal(qcd_ctx* c, const void* S_int, const int src[4], int t_sep, int direction, double tol,
-                            int n_iter, double* corr3, qcd_rhs_stats* st) {
+qcd_status threept_internal(qcd_ctx* c, const void* S_int, const void* S_sink, const int src[4], int t_sep,
+                            int direction, double tol, int n_iter, double* corr3, qcd_rhs_stats* st) {
   const int V = c->g.V, T = c->g.L[0], L3 = V / T;
   const int t0 = src[0];
   const int ts = ((t0 + direction * t_sep) % T + T) % T;
@@ -241,7 +244,7 @@ qcd_status threept_internal(qcd_ctx* c, const void* S_int, const int src[4], int
     {
       // the sequential source lives on the sink time-slice only
       ProfScope ps(c, FAM_CONTRACT, (double)L3 * 3 * 2304, (double)L3 * 36 * 6 * 200 * 8);
-      nucleon_grad::k_dC_dS<<<L3 / ns, 18 * ns, smem, c->stream>>>((const double2*)S_int,
+      nucleon_grad::k_dC_dS<<<L3 / ns, 18 * ns, smem, c->stream>>>((const double2*)S_sink,
                                                                   (const double2*)c->contract.p, V, L3, ns, ts * L3,
                                                                   (double2*)c->wsD[5].p);
       QCD_CUDA_OK(cudaGetLastError());
@@ -250,6 +253,7 @@ qcd_status threept_internal(qcd_ctx* c, const void* S_int, const int src[4], int
           (const double2*)c->wsD[5].p, (double2*)((char*)c->wsD[6].p + f64 * 12 * p), V);
       QCD_CUDA_OK(cudaGetLastError());
     }
+    if (S_sink != S_int) QCD_TRY(smear_fields(c, (char*)c->wsD[6].p + f64 * 12 * p, 12));
   }
   // the 24 sequential propagators, 12 at a time: W = D^-1 eta
   std::vector<double> tols(12, n_iter > 0 ? 1e-300 : tol);
@@ -335,7 +339,7 @@ extern "C" qcd_status qcd_nucleon_3pt(qcd_ctx* c, const double* prop, const int 
   QCD_TRY(devbuf_ensure(c->wsD[4], f64 * 12));
   QCD_TRY(layout_spinor_import(c, prop, c->wsD[4].p, QCD_PREC_F64, 12));
   std::vector<qcd_rhs_stats> st(24);
-  QCD_TRY(threept_internal(c, c->wsD[4].p, src, t_sep, direction, tol, 0, corr3, st.data()));
+  QCD_TRY(threept_internal(c, c->wsD[4].p, c->wsD[4].p, src, t_sep, direction, tol, 0, corr3, st.data()));
   qcd_status worst = QCD_OK;
   for (int r = 0; r < 24; r++) {
     if (stats) stats[r] = st[r];

@@ -30,7 +30,8 @@ EXPORTS = (
     "qcd_nucleon_2pt", "qcd_ama_nucleon_2pt", "qcd_get_clover", "qcd_profile_enable", "qcd_profile_read",
     "qcd_deflation_setup", "qcd_deflation_fields", "qcd_deflation_little_matrix", "qcd_deflation_little",
     "qcd_nucleon_2pt_noalloc", "qcd_autotune", "qcd_fh_forward", "qcd_fh_gradient", "qcd_solve_multi",
-    "qcd_nucleon_3pt", "qcd_ama_nucleon", "qcd_ama_error_model",
+    "qcd_nucleon_3pt", "qcd_ama_nucleon", "qcd_ama_error_model", "qcd_smear_links", "qcd_set_smearing",
+    "qcd_smear_gaussian", "qcd_get_smeared_links",
 )
 
 
@@ -102,6 +103,10 @@ def load_library(path=LIB_PATH):
     L.qcd_nucleon_3pt.argtypes = [vp, vp, ip, i, i, d, dp, ctypes.POINTER(RhsStats)]
     L.qcd_ama_nucleon.argtypes = [vp, ip, i, ctypes.POINTER(AmaParams), dp, dp, dp, dp, ctypes.POINTER(RhsStats)]
     L.qcd_ama_error_model.argtypes = [dp, dp, dp, i, i, i, dp]
+    L.qcd_smear_links.argtypes = [vp, d, i]
+    L.qcd_set_smearing.argtypes = [vp, d, i]
+    L.qcd_smear_gaussian.argtypes = [vp, vp, vp, i]
+    L.qcd_get_smeared_links.argtypes = [vp, vp]
     L.qcd_ama_nucleon_2pt.argtypes = [vp, ip, i, i, d, d, dp, dp, ctypes.POINTER(RhsStats)]
     L.qcd_get_clover.argtypes = [vp, vp]
     L.qcd_nucleon_2pt_noalloc.argtypes = [ip, i, vp, ip, vp, i, vp]
@@ -423,6 +428,34 @@ class Lattice:
                                     g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol),
                                     grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stats))
         return float(grad[0]), float(grad[1])
+
+    def smear_links(self, alpha, n_ape):
+        """APE-smear the spatial links (kept in the context)."""
+        _check(_lib.qcd_smear_links(self._ctx, float(alpha), int(n_ape)))
+
+    def set_smearing(self, kappa_g, n_gauss):
+        """Gaussian source and sink smearing for ama_nucleon (n_gauss = 0: point)."""
+        _check(_lib.qcd_set_smearing(self._ctx, float(kappa_g), int(n_gauss)))
+
+    def smear_gaussian(self, psi):
+        """K psi for a CUDA complex128 tensor of spinors (canonical layout)."""
+        import torch
+        psi = psi.contiguous()
+        n = psi.shape[0] if psi.dim() == 7 else 1
+        out = torch.empty_like(psi)
+        self._after_torch()
+        _check(_lib.qcd_smear_gaussian(self._ctx, _dev_ptr(psi), _dev_ptr(out), n))
+        self._before_torch()
+        return out
+
+    def smeared_links(self):
+        """The APE-smeared gauge field as a CUDA complex128 tensor (T, Z, Y, X, 4, 3, 3)."""
+        import torch
+        out = torch.empty((self.T, self.Z, self.Y, self.X, 4, 3, 3), dtype=torch.complex128, device="cuda")
+        self._after_torch()
+        _check(_lib.qcd_get_smeared_links(self._ctx, _dev_ptr(out)))
+        self._before_torch()
+        return out
 
     def get_clover(self):
         """A(x) as a CUDA complex128 tensor [V, 2, 6, 6]."""
