@@ -205,6 +205,8 @@ void qcd_destroy(qcd_ctx* c) {
   devbuf_free(c->gaugeF);
   devbuf_free(c->cloverD);
   devbuf_free(c->cloverF);
+  devbuf_free(c->gaugeH);
+  devbuf_free(c->cloverH);
   for (int i = 0; i < 8; i++) {
     devbuf_free(c->wsD[i]);
     devbuf_free(c->wsF[i]);

@@ -240,6 +240,28 @@ __global__ void k_spinor_export<float4>(const float4* __restrict__ in, double2* 
   }
 }
 
+// FP16 copies of the FP32 links (full 3x3) and clover term, rounded exactly as
+// the SAP kernel's staging rounds them (one conversion per (re, im) pair)
+__global__ void k_half_fields(const float4* __restrict__ gaugeF, const float4* __restrict__ cloverF, int V,
+                              uint4* __restrict__ gA, uint4* __restrict__ gB, unsigned* __restrict__ gC,
+                              uint4* __restrict__ clH) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  for (int mu = 0; mu < 4; mu++) {
+    const SU3<float> U = FieldsF::load_link(gaugeF, V, mu, s);
+    unsigned h[9];
+    for (int k = 0; k < 9; k++) h[k] = h2_bits(__floats2half2_rn(U.m[k / 3][k % 3].re, U.m[k / 3][k % 3].im));
+    gA[(size_t)mu * V + s] = make_uint4(h[0], h[1], h[2], h[3]);
+    gB[(size_t)mu * V + s] = make_uint4(h[4], h[5], h[6], h[7]);
+    gC[(size_t)mu * V + s] = h[8];
+  }
+  for (int k = 0; k < 9; k++) {
+    const float4 a = cloverF[(size_t)(2 * k) * V + s], b = cloverF[(size_t)(2 * k + 1) * V + s];
+    clH[(size_t)k * V + s] = make_uint4(h2_bits(__floats2half2_rn(a.x, a.y)), h2_bits(__floats2half2_rn(a.z, a.w)),
+                                        h2_bits(__floats2half2_rn(b.x, b.y)), h2_bits(__floats2half2_rn(b.z, b.w)));
+  }
+}
+
 }  // namespace
 
 qcd_status layout_gauge_import(qcd_ctx* c, const double* U_dev) {
@@ -260,6 +282,15 @@ qcd_status layout_clover_build(qcd_ctx* c) {
   ProfScope ps(c, FAM_LAYOUT, (double)V * (576 + 576 + 288), 0.0);
   k_clover_build<<<nblk(V, 128), 128, 0, c->stream>>>((const double2*)c->gaugeD.p, c->g, c->kappa * c->csw,
                                                       (double2*)c->cloverD.p, (float4*)c->cloverF.p);
+  QCD_CUDA_OK(cudaGetLastError());
+  // FP16 copies of links and clover term for the sloppy SAP block solves
+  QCD_TRY(devbuf_ensure(c->gaugeH, (size_t)V * 4 * 36));
+  QCD_TRY(devbuf_ensure(c->cloverH, (size_t)V * 144));
+  uint4* gA = (uint4*)c->gaugeH.p;
+  uint4* gB = gA + 4 * (size_t)V;
+  unsigned* gC = (unsigned*)(gB + 4 * (size_t)V);
+  k_half_fields<<<nblk(V, 128), 128, 0, c->stream>>>((const float4*)c->gaugeF.p, (const float4*)c->cloverF.p, V, gA,
+                                                     gB, gC, (uint4*)c->cloverH.p);
   QCD_CUDA_OK(cudaGetLastError());
   return QCD_OK;
 }

@@ -443,6 +443,12 @@ struct qcd_ctx {
   qcd_solver_params params;
   // fields
   DevBuf gaugeD, gaugeF, cloverD, cloverF;
+  // FP16 copies for the sloppy SAP block solves (layout.cu): links as the nine
+  // (re, im) entries of the full matrix (third row reconstructed in FP32 from
+  // the FP32 rows, then rounded), [4][V] uint4 of entries 0-3, [4][V] uint4 of
+  // entries 4-7, [4][V] uint32 of entry 8 (36 B per link); clover as
+  // [9][V] uint4 of eight FP16 reals (144 B per site)
+  DevBuf gaugeH, cloverH;
   // workspaces (grown on demand, kept until destroy)
   DevBuf wsD[8];      // FP64 spinors (nrhs each)
   DevBuf wsF[8];      // FP32 spinors

@@ -22,6 +22,8 @@
 // increment x in registers.
 #include <string.h>
 
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -384,7 +386,8 @@ template <typename S, bool BF, bool B4, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_sap_sweep_smem(const char* __restrict__ rho_src, char* __restrict__ rho, char* __restrict__ psi,
                      char* __restrict__ delta,
-                     const float4* __restrict__ gauge, const float4* __restrict__ clover, Geom g, SapGeom sg_in,
+                     const float4* __restrict__ gauge, const float4* __restrict__ clover,
+                     const uint4* __restrict__ gaugeH, const uint4* __restrict__ cloverH, Geom g, SapGeom sg_in,
                      int colour, int gather, int psi_init, float kappa, int nmr, int nrhs, const int* mask) {
   SapGeom sg = sg_in;
   if (B4) {
@@ -438,15 +441,38 @@ __global__ void __launch_bounds__(MAXT, MINB)
   c[3] = bz * sg.b[3] + lc[3];
   const int s = ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
 
-  // stage this site's four links (full 3x3) and its clover term
+  // stage this site's four links (full 3x3) and its clover term: 16-bit
+  // copies straight from their FP16 copies in HBM (rounded once at gauge
+  // load, as the FP32 path rounds them here), FP32 copies from the FP32 fields
+  if (std::is_same<S, __half>::value) {
+    const uint4* gB = gaugeH + 4 * (size_t)g.V;
+    const unsigned* gC = (const unsigned*)(gB + 4 * (size_t)g.V);
+    unsigned* lw = (unsigned*)lk_s;
 #pragma unroll
-  for (int mu = 0; mu < 4; mu++) {
-    SU3<float> U = FieldsF::load_link(gauge, g.V, mu, s);
+    for (int mu = 0; mu < 4; mu++) {
+      const uint4 a = __ldg(gaugeH + (size_t)mu * g.V + s), b = __ldg(gB + (size_t)mu * g.V + s);
+      const unsigned h8 = __ldg(gC + (size_t)mu * g.V + s);
+      const unsigned w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, h8};
 #pragma unroll
-    for (int k = 0; k < 9; k++) lk_s[(size_t)(9 * mu + k) * vb + l] = Stage<S>::putc(U.m[k / 3][k % 3]);
+      for (int k = 0; k < 9; k++) lw[(size_t)(9 * mu + k) * vb + l] = w[k];
+    }
+    uint2* cw = (uint2*)cl_s;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      const uint4 v = __ldg(cloverH + (size_t)k * g.V + s);
+      cw[(size_t)(2 * k) * vb + l] = make_uint2(v.x, v.y);
+      cw[(size_t)(2 * k + 1) * vb + l] = make_uint2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      SU3<float> U = FieldsF::load_link(gauge, g.V, mu, s);
+#pragma unroll
+      for (int k = 0; k < 9; k++) lk_s[(size_t)(9 * mu + k) * vb + l] = Stage<S>::putc(U.m[k / 3][k % 3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 18; k++) cl_s[(size_t)k * vb + l] = Stage<S>::put(__ldg(clover + (size_t)k * g.V + s));
   }
-#pragma unroll
-  for (int k = 0; k < 18; k++) cl_s[(size_t)k * vb + l] = Stage<S>::put(__ldg(clover + (size_t)k * g.V + s));
 
   Spinor<float> r = FieldsF::load_spinor(rho_src, g.V, s);
   if (BF) {
@@ -588,6 +614,9 @@ qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, 
                                 : (b4 ? k_sap_sweep_smem<float, false, true, 256, 1>
                                       : k_sap_sweep_smem<float, false, false, 256, 1>);
   const size_t smem_res = (size_t)sg.vb * ((P.sap_half == 2 ? 48 : 96) + (P.sap_half ? 144 + 144 : 288 + 288));
+  // links and clover term read per active site and launch: their FP16 copies
+  // (36 B per link, 144 B clover) for the 16-bit staged blocks, else FP32
+  const double gcb = (resident && P.sap_half) ? 4 * 36.0 + 144.0 : 4 * lb + cb;
   if (resident)
     QCD_CUDA_OK(cudaFuncSetAttribute(kres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res));
   auto issue = [&]() -> qcd_status {
@@ -596,13 +625,13 @@ qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, 
         const int first = cy == 0 && !accumulate;
         const int gather = !(cy == 0 && col == 0);   // no boundary term before the first half-cycle
         const double bytes_rhs = sb * (2 + (first ? 1 : 2) + 1 + (gather ? f_face : 0.0));
-        ProfScope ps(c, fam, half * (nactive * bytes_rhs + 4 * lb + cb),
+        ProfScope ps(c, fam, half * (nactive * bytes_rhs + gcb),
                      half * nactive * (flops_site - (gather ? 0.0 : flops_gather)));
         const char* rin = cy == 0 ? rho_src : rho;   // the first cycle reads the caller's residual
         if (resident)
           kres<<<grid, sg.vb, smem_res, c->stream>>>(rin, rho, psi, delta, (const float4*)gauge, (const float4*)clover,
-                                                     c->g, sg, col, gather, first, (float)c->kappa,
-                                                     P.nmr, nrhs, mask);
+                                                     (const uint4*)c->gaugeH.p, (const uint4*)c->cloverH.p, c->g, sg,
+                                                     col, gather, first, (float)c->kappa, P.nmr, nrhs, mask);
         else
           kern<<<grid, sg.vb, smem, c->stream>>>(rin, rho, psi, delta, gauge, clover, c->g, sg, col,
                                                  gather, first, (typename F::R)c->kappa, P.nmr, nrhs,
@@ -653,7 +682,7 @@ qcd_status launch_sweeps(qcd_ctx* c, const char* rho_src, char* rho, char* psi, 
     for (int col = 0; col < 2; col++) {
       const int first = cy == 0 && !accumulate;
       const int gather = !(cy == 0 && col == 0);
-      bytes += half * (nactive * sb * (2 + (first ? 1 : 2) + 1 + (gather ? f_face : 0.0)) + 4 * lb + cb);
+      bytes += half * (nactive * sb * (2 + (first ? 1 : 2) + 1 + (gather ? f_face : 0.0)) + gcb);
       flops += half * nactive * (flops_site - (gather ? 0.0 : flops_gather));
     }
   ProfScope ps(c, fam, bytes, flops, 2 * P.ncy);
