@@ -378,14 +378,17 @@ qcd_status qcd_nucleon_2pt_noalloc(const int dims[4], int time_bc, const double*
  * spinors; the caller draws them): block Gram-Schmidt, then n_inv rounds of
  * the inverse iteration phi -> M_SAP phi followed by block Gram-Schmidt; then
  * the little Dirac operator A = (phi_k^b, D phi_l^b') (eq. little) on the
- * block and its 8 neighbours, and the FP64 Gauss-Jordan inverses of its
- * diagonal blocks.  1 <= ns <= 32; SAP block extents >= 2 in every
+ * block and its 8 neighbours (tensor-core GEMMs, FP32-accurate products,
+ * FP64 sums and storage), and the FP64 Gauss-Jordan inverses of its
+ * diagonal blocks.  QCD_ERR_TIMEOUT if the tensor-core build gave up waiting
+ * for its matrix multiplies (a bounded wait; nothing is left running).  1 <= ns <= 32; SAP block extents >= 2 in every
  * direction.  Setting new parameters with a different block size discards
  * the subspace.  Returns QCD_ERR_BREAKDOWN if a diagonal block is singular. */
 qcd_status qcd_deflation_setup(qcd_ctx* ctx, const double* init, int ns, int n_inv);
 /* The deflation fields as ns canonical FP64 spinors (device). */
 qcd_status qcd_deflation_fields(qcd_ctx* ctx, double* out);
-/* The little Dirac operator as host FP64 complex [block][9][ns][ns]: part 0
+/* The little Dirac operator (stored in FP64) as host FP64 complex
+ * [block][9][ns][ns]: part 0
  * couples a block to itself, 1 + 2 mu to its neighbour at +mu, 2 + 2 mu to
  * the one at -mu; blocks are numbered ((bt*nbz + bz)*nby + by)*nbx + bx. */
 qcd_status qcd_deflation_little_matrix(qcd_ctx* ctx, double* out);

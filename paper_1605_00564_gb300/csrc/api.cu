@@ -571,13 +571,9 @@ qcd_status qcd_deflation_little_matrix(qcd_ctx* c, double* out) {
     return QCD_ERR_STATE;
   }
   const size_t n = (size_t)dfl_nblk(c) * 9 * dfl_ns(c) * dfl_ns(c);
-  std::vector<float2> h(n);
-  QCD_CUDA_OK(cudaMemcpyAsync(h.data(), dfl_little(c), sizeof(float2) * n, cudaMemcpyDeviceToHost, c->stream));
+  // A is stored in FP64: copy it out as it is
+  QCD_CUDA_OK(cudaMemcpyAsync(out, dfl_little(c), sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
   QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
-  for (size_t i = 0; i < n; i++) {
-    out[2 * i] = h[i].x;
-    out[2 * i + 1] = h[i].y;
-  }
   return QCD_OK;
 }
 

@@ -184,10 +184,10 @@ __global__ void __launch_bounds__(128) k_dfl_ypart(const char* __restrict__ phi,
 }
 
 // ---------------------------------------------------------------------------
-// Per-block GEMMs over the block's sites and spin-colour components:
-//   out[b][k][j] = sum_{y in b, comp} conj(Phi_k(y)) X_j(y)
-// for X = Y parts (little Dirac) or the residuals (projection).  One CTA per
-// block; tiles of TS sites of both operands are staged in shared memory.
+// Per-block projection c[r][b][k] = sum_{y in b, comp} conj(Phi_k(y)) rho_r(y)
+// of the right-hand sides on the deflation fields.  One CTA per block; tiles
+// of TS sites of both operands are staged in shared memory.  (The little
+// Dirac operator itself is built on the tensor cores, dfl_tc.cu.)
 // ---------------------------------------------------------------------------
 constexpr int TS = 8;
 constexpr int GEMM_TPB = 256;
@@ -195,65 +195,6 @@ constexpr int GEMM_TPB = 256;
 __device__ inline Cplx<float> ld_comp(const char* field, int V, int s, int comp) {
   float4 v = __ldg((const float4*)field + (size_t)(comp >> 1) * V + s);
   return (comp & 1) ? cmk(v.z, v.w) : cmk(v.x, v.y);
-}
-
-// Little Dirac operator: A[b][9][ns][ns] (float2) from Phi and the Y parts
-__global__ void __launch_bounds__(GEMM_TPB) k_dfl_little(const char* __restrict__ phi, const char* __restrict__ Y,
-                                                          float2* __restrict__ A, Geom g, BlkGeom bg, int ns) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cplx<float>* Pt = (Cplx<float>*)smem_raw;           // [ns][12][TS]
-  Cplx<float>* Yt = Pt + (size_t)ns * 12 * TS;         // [5][ns][12][TS]
-  __shared__ int face_lo[4][TS], face_hi[4][TS];
-  const int blk = blockIdx.x;
-  const size_t fb = FieldsF::spinor_bytes * (size_t)g.V;
-  const int nout = ns * ns;
-  const int per = (nout + GEMM_TPB - 1) / GEMM_TPB;    // <= 4
-  Cplx<float> acc[4][9];
-  for (int o = 0; o < 4; o++)
-    for (int p = 0; p < 9; p++) acc[o][p] = cmk(0.f, 0.f);
-  for (int t0 = 0; t0 < bg.vb; t0 += TS) {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < ns * 12 * TS; idx += blockDim.x) {
-      int i = idx % TS, comp = (idx / TS) % 12, k = idx / (12 * TS);
-      int lc[4], c[4];
-      int s = blk_site(bg, g, blk, t0 + i, lc, c);
-      Pt[idx] = ld_comp(phi + k * fb, g.V, s, comp);
-#pragma unroll
-      for (int p = 0; p < 5; p++) Yt[(size_t)p * ns * 12 * TS + idx] = ld_comp(Y + ((size_t)p * ns + k) * fb, g.V, s, comp);
-    }
-    if (threadIdx.x < TS) {
-      int lc[4], c[4];
-      blk_site(bg, g, blk, t0 + threadIdx.x, lc, c);
-      for (int mu = 0; mu < 4; mu++) {
-        face_hi[mu][threadIdx.x] = lc[mu] == bg.b[mu] - 1;
-        face_lo[mu][threadIdx.x] = lc[mu] == 0;
-      }
-    }
-    __syncthreads();
-    for (int o = 0; o < per; o++) {
-      int idx = threadIdx.x + o * GEMM_TPB;
-      if (idx >= nout) break;
-      int k = idx / ns, j = idx - k * ns;
-      const Cplx<float>* pk = Pt + (size_t)k * 12 * TS;
-      for (int comp = 0; comp < 12; comp++)
-        for (int i = 0; i < TS; i++) {
-          Cplx<float> a = pk[comp * TS + i];
-          acc[o][0] = acc[o][0] + cdot(a, Yt[((size_t)j * 12 + comp) * TS + i]);
-#pragma unroll
-          for (int mu = 0; mu < 4; mu++) {
-            Cplx<float> y = cdot(a, Yt[((size_t)(1 + mu) * ns * 12 + (size_t)j * 12 + comp) * TS + i]);
-            if (face_hi[mu][i]) acc[o][1 + 2 * mu] = acc[o][1 + 2 * mu] + y;
-            if (face_lo[mu][i]) acc[o][2 + 2 * mu] = acc[o][2 + 2 * mu] + y;
-          }
-        }
-    }
-  }
-  for (int o = 0; o < per; o++) {
-    int idx = threadIdx.x + o * GEMM_TPB;
-    if (idx >= nout) break;
-    for (int p = 0; p < 9; p++)
-      A[((size_t)blk * 9 + p) * nout + idx] = make_float2(acc[o][p].re, acc[o][p].im);
-  }
 }
 
 // Projection c[r][b][k] = (phi_k^b, rho_r) for the unmasked right-hand sides
@@ -340,15 +281,15 @@ __global__ void __launch_bounds__(128) k_dfl_prolong(const char* __restrict__ ph
 
 // ---------------------------------------------------------------------------
 // Diagonal-block inverses by Gauss-Jordan elimination with partial pivoting
-// in FP64 (one 32-thread CTA per block); stored in FP32.
+// in FP64 (one 32-thread CTA per block); stored in FP64.
 // ---------------------------------------------------------------------------
-__global__ void k_dfl_block_inverse(const float2* __restrict__ A, float2* __restrict__ Ainv, int ns, int* singular) {
+__global__ void k_dfl_block_inverse(const double2* __restrict__ A, double2* __restrict__ Ainv, int ns, int* singular) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* M = (double2*)smem_raw;   // [ns][2 ns]
   __shared__ int piv;
   __shared__ double2 fcol[32];       // column col of M before the elimination step
   const int blk = blockIdx.x, w = 2 * ns;
-  const float2* a = A + (size_t)blk * 9 * ns * ns;   // part 0
+  const double2* a = A + (size_t)blk * 9 * ns * ns;   // part 0
   for (int idx = threadIdx.x; idx < ns * w; idx += blockDim.x) {
     int i = idx / w, j = idx - i * w;
     double2 v = make_double2(0, 0);
@@ -400,15 +341,16 @@ __global__ void k_dfl_block_inverse(const float2* __restrict__ A, float2* __rest
   for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
     int i = idx / ns, j = idx - i * ns;
     double2 v = M[i * w + ns + j];
-    Ainv[(size_t)blk * ns * ns + idx] = make_float2((float)v.x, (float)v.y);
+    Ainv[(size_t)blk * ns * ns + idx] = v;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Little operator and little vector algebra.  x, y: float2 [nrhs][nblk][ns].
+// Little operator and little vector algebra.  x, y: float2 [nrhs][nblk][ns];
+// A and the diagonal-block inverses are FP64, the products are summed in FP64.
 // ---------------------------------------------------------------------------
-// y = A x (part = -1: all 9 parts) or y = Ainv x (diagonal blocks only)
-__global__ void k_little_apply(const float2* __restrict__ M, int nparts, const float2* __restrict__ x,
+// y = A x (nparts = 9) or y = Ainv x (nparts = 1, diagonal blocks only)
+__global__ void k_little_apply(const double2* __restrict__ M, int nparts, const float2* __restrict__ x,
                                float2* __restrict__ y, BlkGeom bg, int ns, int nrhs, const int* mask) {
   const int blk = blockIdx.x;
   const int k = threadIdx.x;   // row
@@ -426,17 +368,18 @@ __global__ void k_little_apply(const float2* __restrict__ M, int nparts, const f
   }
   for (int r = 0; r < nrhs; r++) {
     if (mask && !mask[r]) continue;
-    float ar = 0, ai = 0;
+    double ar = 0, ai = 0;
     for (int p = 0; p < nparts; p++) {
-      const float2* row = M + (((size_t)blk * nparts + p) * ns + k) * ns;
+      const double2* row = M + (((size_t)blk * nparts + p) * ns + k) * ns;
       const float2* xv = x + ((size_t)r * bg.nblk + nbr[p]) * ns;
       for (int l = 0; l < ns; l++) {
-        float2 a = __ldg(row + l), v = xv[l];
+        const double2 a = __ldg(row + l);
+        const float2 v = xv[l];
         ar += a.x * v.x - a.y * v.y;
         ai += a.x * v.y + a.y * v.x;
       }
     }
-    y[((size_t)r * bg.nblk + blk) * ns + k] = make_float2(ar, ai);
+    y[((size_t)r * bg.nblk + blk) * ns + k] = make_float2((float)ar, (float)ai);
   }
 }
 
@@ -536,7 +479,7 @@ __global__ void k_little_update(float2* __restrict__ x, float2* __restrict__ res
 struct DflState {
   int ns = 0, ready = 0;
   BlkGeom bg;
-  DevBuf phi, A, Ainv, Y, little, part, tmp;
+  DevBuf phi, A, Ainv, Y, little, part, tmp, flags;
 };
 
 static DflState* dfl_of(qcd_ctx* c) {
@@ -554,6 +497,7 @@ void dfl_free(qcd_ctx* c) {
   devbuf_free(d->little);
   devbuf_free(d->part);
   devbuf_free(d->tmp);
+  devbuf_free(d->flags);
   delete d;
   c->dfl = nullptr;
 }
@@ -565,16 +509,21 @@ void* dfl_phi(qcd_ctx* c) { return c->dfl ? ((DflState*)c->dfl)->phi.p : nullptr
 void* dfl_little(qcd_ctx* c) { return c->dfl ? ((DflState*)c->dfl)->A.p : nullptr; }
 
 qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st);
+qcd_status dfl_little_tc(qcd_ctx* c, const void* phi, const void* Y, double* A, const int b[4], int ns, int* err);
 
-// Little operator and diagonal-block inverses from the current d->phi.
+// Little operator (tensor cores, FP64 store) and diagonal-block inverses
+// (FP64) from the current d->phi.
 static qcd_status dfl_little_build(qcd_ctx* c) {
   DflState* d = dfl_of(c);
   const BlkGeom& bg = d->bg;
   const int ns = d->ns;
   const size_t fb = spinor_bytes(c, QCD_PREC_F32);
   QCD_TRY(devbuf_ensure(d->Y, 5 * fb * ns));
-  QCD_TRY(devbuf_ensure(d->A, sizeof(float2) * (size_t)bg.nblk * 9 * ns * ns));
-  QCD_TRY(devbuf_ensure(d->Ainv, sizeof(float2) * (size_t)bg.nblk * ns * ns));
+  QCD_TRY(devbuf_ensure(d->A, sizeof(double2) * (size_t)bg.nblk * 9 * ns * ns));
+  QCD_TRY(devbuf_ensure(d->Ainv, sizeof(double2) * (size_t)bg.nblk * ns * ns));
+  QCD_TRY(devbuf_ensure(d->flags, 2 * sizeof(int)));
+  int* flags = (int*)d->flags.p;      // [0] singular diagonal block, [1] tensor-core wait timed out
+  QCD_CUDA_OK(cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
   {
     ProfScope ps(c, FAM_DFL, (double)c->g.V * ns * (96 + 5 * 96 + 192 + 288), (double)c->g.V * ns * 1824);
     dim3 grid((c->g.V + 127) / 128, ns);
@@ -582,27 +531,20 @@ static qcd_status dfl_little_build(qcd_ctx* c) {
                                             (float)c->kappa, ns);
     QCD_CUDA_OK(cudaGetLastError());
   }
+  QCD_TRY(dfl_little_tc(c, d->phi.p, d->Y.p, (double*)d->A.p, bg.b, ns, flags + 1));
   {
-    const size_t smem = sizeof(Cplx<float>) * (size_t)6 * ns * 12 * TS;
-    ProfScope ps(c, FAM_DFL, (double)fb * ns * 6, (double)c->g.V * 12.0 * ns * ns * 8 * 5);
-    QCD_CUDA_OK(cudaFuncSetAttribute(k_dfl_little, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_dfl_little<<<bg.nblk, GEMM_TPB, smem, c->stream>>>((const char*)d->phi.p, (const char*)d->Y.p, (float2*)d->A.p,
-                                                          c->g, bg, ns);
+    ProfScope ps(c, FAM_DFL, 16.0 * bg.nblk * ns * ns * 2, 8.0 * bg.nblk * ns * ns * ns * 2);
+    k_dfl_block_inverse<<<bg.nblk, 32, sizeof(double2) * ns * 2 * ns, c->stream>>>((const double2*)d->A.p,
+                                                                                   (double2*)d->Ainv.p, ns, flags);
     QCD_CUDA_OK(cudaGetLastError());
-  }
-  {
-    int* sing = nullptr;
-    QCD_CUDA_OK(cudaMallocAsync((void**)&sing, sizeof(int), c->stream));
-    QCD_CUDA_OK(cudaMemsetAsync(sing, 0, sizeof(int), c->stream));
-    ProfScope ps(c, FAM_DFL, 8.0 * bg.nblk * ns * ns * 2, 8.0 * bg.nblk * ns * ns * ns * 2);
-    k_dfl_block_inverse<<<bg.nblk, 32, sizeof(double2) * ns * 2 * ns, c->stream>>>((const float2*)d->A.p,
-                                                                                   (float2*)d->Ainv.p, ns, sing);
-    QCD_CUDA_OK(cudaGetLastError());
-    int h = 0;
-    QCD_CUDA_OK(cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int h[2] = {0, 0};
+    QCD_CUDA_OK(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
-    QCD_CUDA_OK(cudaFreeAsync(sing, c->stream));
-    if (h) {
+    if (h[1]) {
+      qcd_set_error("the tensor-core little Dirac build timed out waiting for its matrix multiplies");
+      return QCD_ERR_TIMEOUT;
+    }
+    if (h[0]) {
       qcd_set_error("a diagonal block of the little Dirac operator is singular");
       return QCD_ERR_BREAKDOWN;
     }
@@ -720,8 +662,8 @@ qcd_status dfl_low_mode(qcd_ctx* c, const void* rho, void* x, int n, const int* 
     for (int i = 0; i < m; i++) {
       float2* pi = P + vlen * i;
       float2* qi = Q + vlen * i;
-      k_little_apply<<<bg.nblk, ns, 0, c->stream>>>((const float2*)d->Ainv.p, 1, res, pi, bg, ns, n, mask);
-      k_little_apply<<<bg.nblk, ns, 0, c->stream>>>((const float2*)d->A.p, 9, pi, qi, bg, ns, n, mask);
+      k_little_apply<<<bg.nblk, ns, 0, c->stream>>>((const double2*)d->Ainv.p, 1, res, pi, bg, ns, n, mask);
+      k_little_apply<<<bg.nblk, ns, 0, c->stream>>>((const double2*)d->A.p, 9, pi, qi, bg, ns, n, mask);
       if (i > 0) {
         k_little_dots<<<gv, 256, 0, c->stream>>>(Q, vlen, i, qi, N, part, mask);
         k_little_sum<<<dim3(i, n), 256, 0, c->stream>>>(part, i, G, dots, n, mask);
@@ -759,7 +701,7 @@ qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int
   y = x + vlen;
   QCD_CUDA_OK(cudaMemcpyAsync(x, h.data(), sizeof(float2) * vlen, cudaMemcpyHostToDevice, c->stream));
   if (mode == 0) {
-    k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const float2*)d->A.p, 9, x, y, d->bg, d->ns, n, nullptr);
+    k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const double2*)d->A.p, 9, x, y, d->bg, d->ns, n, nullptr);
   } else {
     // reuse the solver on little vectors: the projection is skipped by copying x into the rhs slot
     QCD_TRY(devbuf_ensure(d->little, sizeof(float2) * vlen * (3 + 2 * (size_t)m)));
@@ -777,8 +719,8 @@ qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int
     for (int i = 0; i < m; i++) {
       float2* pi = P + vlen * i;
       float2* qi = Q + vlen * i;
-      k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const float2*)d->Ainv.p, 1, res, pi, d->bg, d->ns, n, nullptr);
-      k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const float2*)d->A.p, 9, pi, qi, d->bg, d->ns, n, nullptr);
+      k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const double2*)d->Ainv.p, 1, res, pi, d->bg, d->ns, n, nullptr);
+      k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const double2*)d->A.p, 9, pi, qi, d->bg, d->ns, n, nullptr);
       if (i > 0) {
         k_little_dots<<<gv, 256, 0, c->stream>>>(Q, vlen, i, qi, N, part, nullptr);
         k_little_sum<<<dim3(i, n), 256, 0, c->stream>>>(part, i, G, dots, n, nullptr);
