@@ -1,13 +1,16 @@
 #!/usr/bin/env python
-"""Benchmark: batched mixed-precision AMA nucleon two-point function, 32^3x64.
+"""Benchmark: batched mixed-precision AMA nucleon two-point function on a
+batch of two lattices, 32^3x64 and 24^3x48.
 
-One step is the whole hot path on one gauge configuration, one call of
-qcd_ama_nucleon_2pt: the 12 spin-colour point sources at each of N_G = 8
+One step is the whole hot path on one gauge configuration of each lattice,
+one call of qcd_ama_nucleon_2pt per lattice (one after the other on one
+stream): the 12 spin-colour point sources at each of N_G = 8
 block-preserving source positions solved with SAP-preconditioned flexible
 GCR to the sloppy tolerance 1e-3, the 12 sources of the first position also
 solved to 1e-10 (N_org = 1), the nucleon contraction of all 9 propagators
-and the AMA combination.  value = solves per second, a solve being one
-spin-colour right-hand side brought to its tolerance (108 per step).
+and the AMA combination.  value = solves per second over the batch, a solve
+being one spin-colour right-hand side brought to its tolerance (108 per
+lattice, 216 per step); the per-lattice rates are reported beside it.
 
 Timing: W warm-up steps, then K steps between CUDA events on the library's
 stream, with a barrier and a synchronize on both sides; the maximum over
@@ -33,9 +36,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "AMA solves/sec on 32^3x64 (batched mixed vs plain FP64); Dslash HBM GB/s vs peak"
 UNIT = "solves/s"
-WORKLOAD = dict(name="prod_32c64_k130", kappa_named=0.1360, n_g=8, n_org=1, sloppy_tol=1e-3, exact_tol=1e-10,
-                block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, sap_half=1, restart_drop=1e-5, max_outer=4000,
-                basis_half=1)
+WORKLOAD = dict(lattices=(("prod_32c64_k130", 0.1360), ("batch2_24c48_k130", 0.1355)), n_g=8, n_org=1,
+                sloppy_tol=1e-3, exact_tol=1e-10, block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=16, sap_half=1,
+                restart_drop=1e-5, max_outer=4000, basis_half=1)
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 sub-partitions x 32)
 
 
@@ -58,29 +61,40 @@ def peaks():
 
 
 def workload_config():
+    """[(name, config, source positions)] of the lattices of the batch."""
     from paper_1605_00564_gb300 import synth
-    cfg = dict(synth.CONFIGS[WORKLOAD["name"]])
-    srcs = synth.ama_source_shifts(cfg["dims"], WORKLOAD["n_g"])
-    return cfg, srcs
+    out = []
+    for name, _ in WORKLOAD["lattices"]:
+        cfg = dict(synth.CONFIGS[name])
+        out.append((name, cfg, synth.ama_source_shifts(cfg["dims"], WORKLOAD["n_g"])))
+    return out
 
 
-def config_json(cfg):
-    T, X, Y, Z = cfg["dims"]
+def lattice_label(dims):
+    T, X, Y, Z = dims
+    return "%d^3x%d" % (X, T) if X == Y == Z else "x".join(map(str, (T, X, Y, Z)))
+
+
+def config_json(lats):
+    first = lats[0][1]
     return {
-        "workload": "AMA nucleon 2pt, %dx%d^3 (T=%d), N_G=%d sloppy (tol %g) + N_org=%d exact (tol %g), "
-                    "12 spin-colour RHS each" % (X, X, T, WORKLOAD["n_g"], WORKLOAD["sloppy_tol"], WORKLOAD["n_org"],
+        "workload": "AMA nucleon 2pt on a batch of %s, each N_G=%d sloppy (tol %g) + N_org=%d exact (tol %g), "
+                    "12 spin-colour RHS each" % (" + ".join("%d^3x%d" % (c["dims"][1], c["dims"][0]) for _, c, _ in lats),
+                                                 WORKLOAD["n_g"], WORKLOAD["sloppy_tol"], WORKLOAD["n_org"],
                                                  WORKLOAD["exact_tol"]),
-        "lattice": [T, X, Y, Z], "kappa": cfg["kappa"], "kappa_named": WORKLOAD["kappa_named"],
-        "kappa_note": "at kappa 0.1360 this synthetic field needs ~600 outer iterations (exact) instead of O(100); "
-                      "kappa lowered to 0.1300 (~150)", "csw": cfg["csw"], "gauge": "U=exp(i*%g*H) seeded" % cfg["eps"],
+        "lattices": [list(c["dims"]) for _, c, _ in lats],
+        "kappa": [c["kappa"] for _, c, _ in lats], "kappa_named": [k for _, k in WORKLOAD["lattices"]],
+        "kappa_note": "on these synthetic fields the named kappas (0.1360, 0.1355) need ~600 / ~390 outer "
+                      "iterations for a 1e-10 solve instead of O(100); kappa lowered to 0.1300 on both (~170 / ~130)",
+        "csw": first["csw"], "gauge": "U=exp(i*%g*H) seeded" % first["eps"],
         "solver": "FGCR(nkv=%d, restart_drop=%g, %s) + SAP(block %s, ncy=%d, nmr=%d, FP32, %s block copies, "
                   "CUDA graphs); exact solves start from the sloppy solution" % (
             WORKLOAD["nkv"], WORKLOAD["restart_drop"],
             "sloppy solves: FP16+scale Krylov images" if WORKLOAD["basis_half"] else "FP32 Krylov images",
             "x".join(map(str, WORKLOAD["block"])), WORKLOAD["ncy"],
             WORKLOAD["nmr"], "FP16" if WORKLOAD["sap_half"] else "FP32"),
-        "rhs_per_step": 12 * (WORKLOAD["n_g"] + WORKLOAD["n_org"]),
-        "l2": "inputs larger than L2 (FP32 gauge+clover 1.0 GB), no flush",
+        "rhs_per_step": 12 * (WORKLOAD["n_g"] + WORKLOAD["n_org"]) * len(lats),
+        "l2": "inputs larger than L2 (FP32 gauge+clover 1.0 GB at 32^3x64), no flush",
     }
 
 
@@ -161,28 +175,31 @@ def oracle_sample(max_iter=8, parallel=True):
     Time per iteration of the oracle's unpreconditioned GCR (each iteration one
     application of its D plus the Gram-Schmidt; the solve's initial and restart
     applications of D are charged to the sampled iterations) measured on a
-    16^3x32 field of the workload's distribution, scaled by the volume (x16) to
-    32^3x64; times the iteration counts of completed oracle solves on that
+    16^3x32 field of the workload's distribution, scaled by each lattice's
+    volume; times the iteration counts of completed oracle solves on that
     16^3x32 field (oracle/gcr_iteration_counts.json: to 1e-3, and to 1e-10 from
-    the 1e-3 solution, as the benchmark's exact solves start).  Measured in one
-    process (numpy's own threads), and with one single-threaded process per
-    host core working at once.  Returns (solves/s on all cores, description,
-    cores, solves/s of the single process)."""
+    the 1e-3 solution, as the benchmark's exact solves start), for every
+    lattice of the batch.  Measured in one process (numpy's own threads), and
+    with one single-threaded process per host core working at once.  Returns
+    (solves/s on all cores, description, cores, solves/s of the single
+    process)."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
-    from paper_1605_00564_gb300 import synth
-    cfg, _ = workload_config()
+    lats = workload_config()
+    cfg = lats[0][1]
     counts = json.load(open(os.path.join(ROOT, "oracle", "gcr_iteration_counts.json")))
     dims = tuple(counts["dims"])
-    vol_ratio = float(np.prod(cfg["dims"])) / float(np.prod(dims))
+    # the batch's cost in units of one iteration on the sampled field: each
+    # lattice's volume ratio times its solves' iterations
+    n_s, n_e = counts["iters_sloppy"], counts["iters_exact_from_sloppy"]
+    iters_step = 12 * WORKLOAD["n_g"] * n_s + 12 * WORKLOAD["n_org"] * n_e
+    vol_iters = sum(float(np.prod(c["dims"])) / float(np.prod(dims)) * iters_step for _, c, _ in lats)
+    solves = 12 * (WORKLOAD["n_g"] + WORKLOAD["n_org"]) * len(lats)
     job = (dims, cfg["eps"], cfg["csw"], cfg["kappa"], counts["seed"], max_iter)
     wall1, cpu1, its1 = _oracle_iteration_worker(job)
     threads1 = max(1, int(round(cpu1 / max(wall1, 1e-9))))
-    t_iter1 = wall1 / its1 * vol_ratio
-    n_s, n_e = counts["iters_sloppy"], counts["iters_exact_from_sloppy"]
-    solves = 12 * (WORKLOAD["n_g"] + WORKLOAD["n_org"])
-    iters_step = 12 * WORKLOAD["n_g"] * n_s + 12 * WORKLOAD["n_org"] * n_e
-    rate1 = solves / (t_iter1 * iters_step)
+    t_iter1 = wall1 / its1                      # per iteration on the sampled field
+    rate1 = solves / (t_iter1 * vol_iters)
     cores, rate_all, t_iter_all = 1, rate1, t_iter1
     if parallel:
         try:
@@ -194,7 +211,6 @@ def oracle_sample(max_iter=8, parallel=True):
         os.environ.update({k: "1" for k in keys})
         try:
             with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
-                w0 = time.perf_counter()
                 res = list(ex.map(_oracle_iteration_worker, [job] * cores))
         finally:
             for k, v in saved.items():
@@ -203,14 +219,15 @@ def oracle_sample(max_iter=8, parallel=True):
                 else:
                     os.environ[k] = v
         # aggregate: cores solves in flight, each at its own per-iteration time
-        t_iter_all = float(np.mean([w / it for w, _, it in res])) * vol_ratio
-        rate_all = cores * solves / (t_iter_all * iters_step)
+        t_iter_all = float(np.mean([w / it for w, _, it in res]))
+        rate_all = cores * solves / (t_iter_all * vol_iters)
     desc = ("oracle.solve.gcr (unpreconditioned restarted GCR, FP64 numpy): %d iterations timed on a 16^3x32 field "
-            "of the workload's distribution, scaled x%d to 32^3x64: %.2f s per iteration in one process (%d threads)"
-            "%s; iteration counts of completed oracle solves on that field: %d to %g, %d more to %g from there "
-            "(oracle/gcr_iteration_counts.json); value = %d solves / (96 x %d + 12 x %d iterations)%s" % (
-                max_iter, vol_ratio, t_iter1, threads1,
-                (", %.2f s per iteration with %d single-threaded processes at once" % (t_iter_all, cores))
+            "of the workload's distribution: %.3f s per iteration in one process (%d threads)%s; per lattice of the "
+            "batch the time per iteration scaled by its volume; iteration counts of completed oracle solves on the "
+            "16^3x32 field: %d to %g, %d more to %g from there (oracle/gcr_iteration_counts.json, used for both "
+            "lattices); value = %d solves / (sum over lattices of volume ratio x (96 x %d + 12 x %d) iterations)%s" % (
+                max_iter, t_iter1, threads1,
+                (", %.3f s per iteration with %d single-threaded processes at once" % (t_iter_all, cores))
                 if parallel else "", n_s, WORKLOAD["sloppy_tol"], n_e, WORKLOAD["exact_tol"], solves, n_s, n_e,
                 (" x %d processes" % cores) if parallel else ""))
     return rate_all, desc, cores, rate1
@@ -312,60 +329,94 @@ def run_ours(args):
     from paper_1605_00564_gb300 import synth
     ws, rank, local = dist_init()
     torch.cuda.set_device(local)
-    cfg, srcs = workload_config()
-    seed = rank_seed(cfg["seed"], rank)       # each rank: its own configuration
-    U = synth.gauge_field(cfg["dims"], cfg["eps"], seed)
-    lat = Lattice(cfg["dims"], stream=torch.cuda.Stream())   # own stream: SAP applications replay CUDA graphs
-    lat.load_gauge(U, cfg["csw"], cfg["kappa"], -1)
-    lat.set_params(block=WORKLOAD["block"], ncy=WORKLOAD["ncy"], nmr=WORKLOAD["nmr"], nkv=WORKLOAD["nkv"],
-                   precision="f32", sap_half=WORKLOAD["sap_half"], restart_drop=WORKLOAD["restart_drop"],
-                   max_outer=WORKLOAD["max_outer"], basis_half=WORKLOAD["basis_half"])
+    lats_cfg = workload_config()
+    # one stream for the batch (non-default: SAP applications replay CUDA graphs)
+    stream = torch.cuda.Stream()
+    lats, fields = [], []
+    for name, cfg, srcs in lats_cfg:
+        seed = rank_seed(cfg["seed"], rank)       # each rank: its own configurations
+        U = synth.gauge_field(cfg["dims"], cfg["eps"], seed)
+        lat = Lattice(cfg["dims"], stream=stream)
+        lat.load_gauge(U, cfg["csw"], cfg["kappa"], -1)
+        lat.set_params(block=WORKLOAD["block"], ncy=WORKLOAD["ncy"], nmr=WORKLOAD["nmr"], nkv=WORKLOAD["nkv"],
+                       precision="f32", sap_half=WORKLOAD["sap_half"], restart_drop=WORKLOAD["restart_drop"],
+                       max_outer=WORKLOAD["max_outer"], basis_half=WORKLOAD["basis_half"])
+        lats.append(lat)
+        fields.append(U)
     n_ex = WORKLOAD["n_org"]
-    step = lambda: lat.ama_nucleon_2pt(srcs, n_ex, WORKLOAD["sloppy_tol"], WORKLOAD["exact_tol"])
+    per_lat = 12 * (WORKLOAD["n_g"] + n_ex)
+    solves = per_lat * len(lats)
+
+    def step():
+        return [lat.ama_nucleon_2pt(srcs, n_ex, WORKLOAD["sloppy_tol"], WORKLOAD["exact_tol"])
+                for lat, (_, _, srcs) in zip(lats, lats_cfg)]
+
     for _ in range(args.warmup):
         step()
-    stream = lat.stream
     clocks = Clocks(local)
     barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
-    lat.profile(True)
+    for lat in lats:
+        lat.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # per-lattice time inside the step (events between the two AMA calls)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(len(lats) + 1)]
+    lat_ms = [0.0] * len(lats)
     e0.record(stream)
-    stats = None
+    results = None
     for _ in range(args.steps):
-        ama, allc, stats = step()
+        results = []
+        marks[0].record(stream)
+        for i, (lat, (_, _, srcs)) in enumerate(zip(lats, lats_cfg)):
+            results.append(lat.ama_nucleon_2pt(srcs, n_ex, WORKLOAD["sloppy_tol"], WORKLOAD["exact_tol"]))
+            marks[i + 1].record(stream)
+        torch.cuda.synchronize()
+        for i in range(len(lats)):
+            lat_ms[i] += marks[i].elapsed_time(marks[i + 1])
     e1.record(stream)
     torch.cuda.synchronize()
-    prof = lat.profile_read()
-    lat.profile(False)
+    prof = {}
+    for lat in lats:
+        for k, v in lat.profile_read().items():
+            acc = prof.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+            for f in acc:
+                acc[f] += v[f]
+        lat.profile(False)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     barrier(ws)
     ms_max = max_over_ranks(ms, ws)
-    solves = 12 * (WORKLOAD["n_g"] + n_ex)
     value = ws * solves * args.steps / (ms_max / 1e3)
 
-    # end to end through the C-ABI with host buffers: gauge field H2D from
-    # pinned memory, correlators D2H, every step
-    Upin = torch.empty(U.shape, dtype=torch.complex128, pin_memory=True)
-    Upin.numpy()[...] = U
-    Uh = Upin.numpy()
+    # end to end through the C-ABI with host buffers: each lattice's gauge field
+    # H2D from pinned memory, the correlators D2H, every step
+    pinned = []
+    for U in fields:
+        Upin = torch.empty(U.shape, dtype=torch.complex128, pin_memory=True)
+        Upin.numpy()[...] = U
+        pinned.append(Upin.numpy())
     n_e2e = max(1, min(args.steps, 3))
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    out_bytes = 0
     for _ in range(n_e2e):
-        lat.load_gauge(Uh, cfg["csw"], cfg["kappa"], -1)
-        step()
+        out_bytes = 0
+        for lat, Uh, (_, cfg, srcs) in zip(lats, pinned, lats_cfg):
+            lat.load_gauge(Uh, cfg["csw"], cfg["kappa"], -1)
+            ama, allc, _ = lat.ama_nucleon_2pt(srcs, n_ex, WORKLOAD["sloppy_tol"], WORKLOAD["exact_tol"])
+            out_bytes += ama.nbytes + allc.nbytes + 12 * (len(srcs) + n_ex) * 24
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e = {"value": ws * solves * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes + 16 * len(srcs)),
-           "d2h_bytes_per_step": int(ama.nbytes + allc.nbytes + 12 * (len(srcs) + n_ex) * 24), "steps": n_e2e}
+    e2e = {"value": ws * solves * n_e2e / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(U.nbytes for U in fields) + sum(16 * len(c[2]) for c in lats_cfg)),
+           "d2h_bytes_per_step": int(out_bytes), "steps": n_e2e}
 
-    # Dslash bandwidth (the metric's second part): FP32, 1 and 12 RHS, kernel time
+    # Dslash bandwidth (the metric's second part): FP32, 1 and 12 RHS on 32^3x64, kernel time
     pk = peaks()
     dsl = {}
+    lat = lats[0]
     for n in (1, 12):
         psi = torch.randn(lat.spinor_shape(n), dtype=torch.complex128, device="cuda")
         torch.cuda.synchronize()
@@ -379,38 +430,41 @@ def run_ours(args):
         dsl["f32_nrhs%d" % n] = {"gbs": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 3),
                                  "us_per_launch": round(1e3 * p["ms"] / p["launches"], 1)}
         del psi
-    lat.profile(False)
 
-    # plain single-RHS FP64 SAP-GCR at the same accuracy, measured: one point
-    # source (spin 0, colour 0 of the first position) solved alone with every
-    # kernel in FP64 to the sloppy tolerance, then from that solution to the
-    # exact tolerance (as the batched path's exact solves start); the step's 96
-    # sloppy and 12 exact solves at those times
+    # plain single-RHS FP64 SAP-GCR at the same accuracy, measured per lattice:
+    # one point source (spin 0, colour 0 of the first position) solved alone with
+    # every kernel in FP64 to the sloppy tolerance, then from that solution to
+    # the exact tolerance (as the batched path's exact solves start); each
+    # lattice's 96 sloppy and 12 exact solves at those times
     plain = None
     if rank == 0 and not args.skip_plain:
-        lat.set_params(precision="f64", rhs_tile=1, restart_drop=WORKLOAD["restart_drop"], basis_half=0)
-        e = torch.from_numpy(synth.point_sources(cfg["dims"], srcs[0])[:1]).cuda()
-        lat.solve(e, 0.5)                     # warm-up: workspaces, graphs
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        psi_s, st_s = lat.solve(e, WORKLOAD["sloppy_tol"])
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        _, st_e = lat.solve(e, WORKLOAD["exact_tol"], psi0=psi_s)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        t_s, t_e = t1 - t0, t2 - t1
-        t_plain = 12 * WORKLOAD["n_g"] * t_s + 12 * n_ex * t_e
+        t_plain, hows = 0.0, []
+        for lat, (_, cfg, srcs) in zip(lats, lats_cfg):
+            lat.set_params(precision="f64", rhs_tile=1, restart_drop=WORKLOAD["restart_drop"], basis_half=0)
+            e = torch.from_numpy(synth.point_sources(cfg["dims"], srcs[0])[:1]).cuda()
+            lat.solve(e, 0.5)                     # warm-up: workspaces, graphs
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            psi_s, st_s = lat.solve(e, WORKLOAD["sloppy_tol"])
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, st_e = lat.solve(e, WORKLOAD["exact_tol"], psi0=psi_s)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            t_s, t_e = t1 - t0, t2 - t1
+            t_plain += 12 * WORKLOAD["n_g"] * t_s + 12 * n_ex * t_e
+            hows.append("%s: %.2f s to %g (%d GCR iterations, true residual %.2e), then %.2f s from there to %g "
+                        "(%d iterations, %.2e)" % (lattice_label(cfg["dims"]), t_s, WORKLOAD["sloppy_tol"],
+                                                   st_s[0]["outer_iters"], st_s[0]["true_rel_residual"], t_e,
+                                                   WORKLOAD["exact_tol"], st_e[0]["outer_iters"],
+                                                   st_e[0]["true_rel_residual"]))
+            lat.set_params(precision="f32", rhs_tile=0, max_outer=WORKLOAD["max_outer"],
+                           restart_drop=WORKLOAD["restart_drop"], basis_half=WORKLOAD["basis_half"])
         plain = {"value": round(solves / t_plain, 4), "unit": UNIT,
-                 "how": "FP64 SAP-GCR (same kernels, FP64 throughout), one RHS at a time, measured: %.2f s to %g "
-                        "(%d GCR iterations, true residual %.2e), then %.2f s from there to %g (%d iterations, %.2e); "
-                        "value = %d solves / (%d x %.2f s + %d x %.2f s)" % (
-                            t_s, WORKLOAD["sloppy_tol"], st_s[0]["outer_iters"], st_s[0]["true_rel_residual"],
-                            t_e, WORKLOAD["exact_tol"], st_e[0]["outer_iters"], st_e[0]["true_rel_residual"],
-                            solves, 12 * WORKLOAD["n_g"], t_s, 12 * n_ex, t_e),
+                 "how": "FP64 SAP-GCR (same kernels, FP64 throughout), one RHS at a time, measured per lattice: " +
+                        "; ".join(hows) + "; value = %d solves / sum over lattices of (96 sloppy + 12 exact) solve "
+                        "times" % solves,
                  "mixed_over_plain": round(value / ws / (solves / t_plain), 2)}
-        lat.set_params(precision="f32", rhs_tile=0, max_outer=WORKLOAD["max_outer"],
-                       restart_drop=WORKLOAD["restart_drop"], basis_half=WORKLOAD["basis_half"])
 
     roof = roofline(prof, ms, clk, peaks())
 
@@ -421,21 +475,26 @@ def run_ours(args):
                "single_process_value": round(v1, 6)}
 
     launches = sum(p["launches"] for p in prof.values())
-    iters = [s["outer_iters"] for s in stats]
+    per = {}
+    for (_, cfg, _), (ama, allc, stats), lms in zip(lats_cfg, results, lat_ms):
+        iters = [s["outer_iters"] for s in stats]
+        per[lattice_label(cfg["dims"])] = {
+            "solves_per_s": round(per_lat * args.steps / (lms / 1e3), 3), "ms_per_step": round(lms / args.steps, 1),
+            "gcr_iters_sloppy": [min(iters[:12 * WORKLOAD["n_g"]]), max(iters[:12 * WORKLOAD["n_g"]])],
+            "gcr_iters_exact": [min(iters[12 * WORKLOAD["n_g"]:]), max(iters[12 * WORKLOAD["n_g"]:])],
+            "max_true_residual_exact": max(s["true_rel_residual"] for s in stats[12 * WORKLOAD["n_g"]:])}
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": config_json(cfg), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "config": config_json(lats_cfg), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk, "dslash": dsl, "plain_fp64": plain,
-        "solver": {"gcr_iters_sloppy": [min(iters[:12 * WORKLOAD["n_g"]]), max(iters[:12 * WORKLOAD["n_g"]])],
-                   "gcr_iters_exact": [min(iters[12 * WORKLOAD["n_g"]:]), max(iters[12 * WORKLOAD["n_g"]:])],
-                   "max_true_residual_exact": max(s["true_rel_residual"] for s in stats[12 * WORKLOAD["n_g"]:]),
-                   "kernel_ms": {k: round(v["ms"] / args.steps, 1) for k, v in prof.items()}},
+        "solver": {"per_lattice": per, "kernel_ms": {k: round(v["ms"] / args.steps, 1) for k, v in prof.items()}},
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
-    lat.close()
+    for lat in lats:
+        lat.close()
 
 
 def run_reference(args):
@@ -446,7 +505,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cfg, _ = workload_config()
+    lats_cfg = workload_config()
     vals = []
     desc, cores = "", 1
     for _ in range(args.warmup):
@@ -460,7 +519,7 @@ def run_reference(args):
     out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": config_json(cfg),
+           "config": config_json(lats_cfg),
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

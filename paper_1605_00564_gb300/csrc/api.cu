@@ -218,6 +218,7 @@ void qcd_destroy(qcd_ctx* c) {
   devbuf_free(c->contract);
   devbuf_free(c->stage);
   devbuf_free(c->guess);
+  devbuf_free(c->small);
   devbuf_free(c->gaugeS);
   devbuf_free(c->smearbuf[0]);
   devbuf_free(c->smearbuf[1]);
@@ -405,16 +406,11 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* c, const int* src, int n_src, int n_exac
   double2* cd = part + npart;
   std::vector<int> sites(12 * spt);
   std::vector<double> tols(12 * spt);
-  int* d_sites = nullptr;
-  QCD_CUDA_OK(cudaMalloc(&d_sites, sizeof(int) * 12 * spt));
+  // the source sites live in a context workspace (no allocation once it is large enough)
+  QCD_TRY(devbuf_ensure(c->small, sizeof(int) * 12 * spt));
+  int* d_sites = (int*)c->small.p;
   DevBuf& guess = c->guess;   // sloppy propagators of the exact-solve sources
-  {
-    qcd_status g = devbuf_ensure(guess, spinor_bytes(c, QCD_PREC_F64) * 12 * n_exact);
-    if (g != QCD_OK) {
-      cudaFree(d_sites);
-      return g;
-    }
-  }
+  QCD_TRY(devbuf_ensure(guess, spinor_bytes(c, QCD_PREC_F64) * 12 * n_exact));
   qcd_status rc = QCD_OK;
   for (int j0 = 0; j0 < njobs && rc == QCD_OK; j0 += spt) {
     // jobs of one tile share a tolerance: do not mix sloppy and exact
@@ -482,7 +478,6 @@ qcd_status qcd_ama_nucleon_2pt(qcd_ctx* c, const int* src, int n_src, int n_exac
     }
   }
   cudaStreamSynchronize(c->stream);
-  cudaFree(d_sites);
   if (rc != QCD_OK) return rc;
   // O_AMA = (1/N_org) sum_f [O^f - O_appx^f] + (1/N_G) sum_g O_appx^g
   for (int k = 0; k < 4 * T; k++) {

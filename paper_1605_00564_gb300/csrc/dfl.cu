@@ -696,9 +696,9 @@ qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int
   const size_t vlen = (size_t)N * n;
   std::vector<float2> h(vlen);
   for (size_t i = 0; i < vlen; i++) h[i] = make_float2((float)in[2 * i], (float)in[2 * i + 1]);
-  float2 *x = nullptr, *y = nullptr;
-  QCD_CUDA_OK(cudaMallocAsync((void**)&x, sizeof(float2) * vlen * 2, c->stream));
-  y = x + vlen;
+  QCD_TRY(devbuf_ensure(d->tmp, sizeof(float2) * vlen * 2));
+  float2* x = (float2*)d->tmp.p;
+  float2* y = x + vlen;
   QCD_CUDA_OK(cudaMemcpyAsync(x, h.data(), sizeof(float2) * vlen, cudaMemcpyHostToDevice, c->stream));
   if (mode == 0) {
     k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const double2*)d->A.p, 9, x, y, d->bg, d->ns, n, nullptr);
@@ -738,7 +738,6 @@ qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int
   QCD_CUDA_OK(cudaGetLastError());
   QCD_CUDA_OK(cudaMemcpyAsync(h.data(), y, sizeof(float2) * vlen, cudaMemcpyDeviceToHost, c->stream));
   QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
-  QCD_CUDA_OK(cudaFreeAsync(x, c->stream));
   for (size_t i = 0; i < vlen; i++) {
     out[2 * i] = h[i].x;
     out[2 * i + 1] = h[i].y;

@@ -187,8 +187,8 @@ extern "C" qcd_status qcd_fh_gradient(qcd_ctx* c, const double* prop, const int 
   // S in Wilson normalisation is the input prop; (g3 g5) S into wsD[0]
   QCD_TRY(gamma_apply(c, c->wsD[4].p, c->wsD[0].p, 1, 1.0, 12));
   // dots per column: <Y_u, S>, <Y_d, S>, <Y_u, G S>, <Y_d, G S>
-  double* dd = nullptr;
-  QCD_CUDA_OK(cudaMallocAsync((void**)&dd, sizeof(double2) * 48, c->stream));
+  QCD_TRY(devbuf_ensure(c->small, sizeof(double2) * 48));
+  double* dd = (double*)c->small.p;
   const char* Yu = (const char*)c->wsD[5].p;
   const char* Yd = Yu + f64 * 12;
   QCD_TRY(blas_dot(c, Yu, QCD_PREC_F64, c->wsD[4].p, QCD_PREC_F64, 12, dd, nullptr));
@@ -198,7 +198,6 @@ extern "C" qcd_status qcd_fh_gradient(qcd_ctx* c, const double* prop, const int 
   std::vector<double> h(96);
   QCD_CUDA_OK(cudaMemcpyAsync(h.data(), dd, sizeof(double) * 96, cudaMemcpyDeviceToHost, c->stream));
   QCD_CUDA_OK(cudaStreamSynchronize(c->stream));
-  QCD_CUDA_OK(cudaFreeAsync(dd, c->stream));
   double dm = 0, dl = 0;
   for (int r = 0; r < 12; r++) {
     dm -= h[2 * r] + h[24 + 2 * r];          // -Re <Y_u + Y_d, S>

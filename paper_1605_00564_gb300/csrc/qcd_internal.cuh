@@ -459,6 +459,7 @@ struct qcd_ctx {
   DevBuf contract;    // per-site contraction values
   DevBuf stage;       // staging for host <-> device copies
   DevBuf guess;       // sloppy solutions reused as initial guesses of exact solves
+  DevBuf small;       // small per-call arrays (source sites, dot products), kept between calls
   double* host_scal = nullptr;   // pinned mirror of scalars
   size_t host_scal_bytes = 0;
   void* dfl = nullptr;           // deflation state (dfl.cu)

@@ -38,6 +38,9 @@ CONFIGS = {
     # workload is specified with); 0.1300 needs ~150
     "prod_32c64_k130": dict(dims=(64, 32, 32, 32), eps=0.15, csw=1.9, kappa=0.1300, seed=160500565),
     "batch2_24c48":    dict(dims=(48, 24, 24, 24), eps=0.15, csw=1.9, kappa=0.1355, seed=160500566),
+    # same field at kappa = 0.1300, as for 32^3x64: at 0.1355 the 1e-10 solves
+    # need ~390 SAP-GCR iterations on this field, at 0.1300 ~130
+    "batch2_24c48_k130": dict(dims=(48, 24, 24, 24), eps=0.15, csw=1.9, kappa=0.1300, seed=160500566),
     "defl_48c96":      dict(dims=(96, 48, 48, 48), eps=0.12, csw=1.9, kappa=0.1362, seed=160500567),
 }
 
