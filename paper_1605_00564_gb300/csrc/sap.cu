@@ -545,7 +545,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
       cmac(x.c[k], alpha, r.c[k]);
       cmac(r.c[k], malpha, p.c[k]);
     }
-    __syncthreads();
+    // every thread read its neighbours' residual for p before the barrier
+    // above, so the new residual can be stored now; the next step's first
+    // barrier orders the store (and the reads of red[]) before any later use
     rs_store<BF>(r_s, vb, l, r);
   }
 

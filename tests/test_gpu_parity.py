@@ -70,6 +70,20 @@ def test_dirac_fp32(request, which):
     assert elem_err(out[:, edge], ref[:, edge]) < 5e-6
 
 
+@pytest.mark.parametrize("which", ["ragged", "slabbed"])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 5e-6)])
+def test_dirac_many_rhs(request, which, prec, tol):
+    """13 RHS, an odd count: the RHS of one run of sites are 13 adjacent CTAs."""
+    lat, op, _ = request.getfixturevalue(which)
+    psi = synth.random_spinor(lat.dims, 13, nrhs=13)
+    for dagger in (False, True):
+        out = to_host(lat.apply_dirac(to_dev(psi), dagger=dagger, precision=prec))
+        ref = np.stack([op.D(p, dagger=dagger) for p in psi])
+        assert record("dirac_%s_%s_n13_%d" % (prec, which, dagger), elem_err(out, ref)) < tol
+        edge = [0, lat.T - 1]
+        assert elem_err(out[:, edge], ref[:, edge]) < tol
+
+
 def test_dirac_periodic_time():
     lat, op, _ = make_lattice((4, 4, 4, 6), eps=0.3, csw=1.0, kappa=0.125, seed=5, bc_t=1)
     psi = synth.random_spinor(lat.dims, 9)
