@@ -68,7 +68,7 @@ typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
  *   nkv         GCR Krylov vectors per restart cycle (<= 32).
  *   max_outer   cap on GCR iterations (preconditioner applications) per RHS.
  *   restart_drop  a restart cycle ends when the recursive residual fell by
- *               this factor (0 = only at nkv); the true FP64 residual is then
+ *               this factor (0 = only at nkv); the true residual is then
  *               recomputed.  Used with the mixed-precision policy.
  *   precision   QCD_PREC_F32: FP64 outer vectors and true residuals, FP32 SAP
  *               and Krylov basis (mixed precision, Sec. 2.2 last paragraph);
@@ -98,8 +98,16 @@ typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1 } qcd_precision;
  *               instead of 96; arithmetic stays FP32).  The recursive residual
  *               then carries the FP16 rounding (about 3e-4 relative), so it is
  *               meant for sloppy tolerances; convergence is still decided by
- *               the FP64 true residual.  qcd_ama_nucleon_2pt applies it to the
+ *               the true residual.  qcd_ama_nucleon_2pt applies it to the
  *               sloppy solves only.  0 = FP32 storage.  Ignored for QCD_PREC_F64.
+ *   resid_f32_tol  QCD_PREC_F32 only: a tile of right-hand sides whose every
+ *               tolerance is >= resid_f32_tol evaluates its true residuals
+ *               eta - D psi with the FP32 operator (psi rounded to FP32, the
+ *               difference taken in FP64).  The rounding of D psi, about
+ *               1e-7 |D| |psi|, stays far below such a stopping tolerance,
+ *               while FP64 arithmetic runs at 1/64 of the FP32 rate on this
+ *               GPU.  0 = FP64 true residuals always (the default).  A value
+ *               below 1e-4 is rejected.
  */
 typedef struct {
   int block[4];
@@ -116,6 +124,7 @@ typedef struct {
   int dfl_gen_iters;
   int graphs;
   int basis_half;
+  double resid_f32_tol;
 } qcd_solver_params;
 
 /* Per right-hand-side outcome of a solve. */
@@ -123,7 +132,8 @@ typedef struct {
   int status;                 /* QCD_OK or QCD_ERR_NOT_CONVERGED / ..._NONFINITE */
   int outer_iters;            /* GCR iterations (preconditioner applications) */
   int restarts;               /* true-residual recomputations */
-  double true_rel_residual;   /* FP64 ||eta - D psi|| / ||eta|| at exit */
+  double true_rel_residual;   /* ||eta - D psi|| / ||eta|| at exit (FP64 sums;
+                                 D psi in FP64, or FP32 under resid_f32_tol) */
 } qcd_rhs_stats;
 
 /* Message for a status code (static string). */
@@ -147,7 +157,7 @@ qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int U_on_device, double
 /* The solver's tunables (Sec. 2.2 and the struct above).
  * Default parameters: block 4^4, ncy 5, nmr 4, nkv 16, max_outer 2000,
  * restart_drop 1e-5, precision F32, rhs_tile 0, sap_half 0, dfl 1,
- * dfl_little_iters 16, dfl_gen_iters 0, graphs 1, basis_half 0. */
+ * dfl_little_iters 16, dfl_gen_iters 0, graphs 1, basis_half 0, resid_f32_tol 0. */
 void qcd_default_params(qcd_solver_params* p);
 qcd_status qcd_set_params(qcd_ctx* ctx, const qcd_solver_params* p);
 

@@ -123,6 +123,8 @@ qcd_status validate_params(const qcd_ctx* c, const qcd_solver_params* p) {
   ARG_CHECK(p->dfl_gen_iters >= 0 && p->dfl_gen_iters <= 64, "dfl_gen_iters must be in [0, 64]");
   ARG_CHECK(p->graphs == 0 || p->graphs == 1, "graphs must be 0 or 1");
   ARG_CHECK(p->basis_half == 0 || p->basis_half == 1, "basis_half must be 0 or 1");
+  ARG_CHECK(p->resid_f32_tol == 0 || (p->resid_f32_tol >= 1e-4 && p->resid_f32_tol < 1),
+            "resid_f32_tol must be 0 or in [1e-4, 1)");
   return QCD_OK;
 }
 
@@ -167,6 +169,7 @@ void qcd_default_params(qcd_solver_params* p) {
   p->dfl_gen_iters = 0;
   p->graphs = 1;
   p->basis_half = 0;
+  p->resid_f32_tol = 0;
 }
 
 qcd_status qcd_create(qcd_ctx** out, const int dims[4], void* cuda_stream) {

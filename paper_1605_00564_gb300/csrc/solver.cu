@@ -178,14 +178,24 @@ qcd_status solver_run(qcd_ctx* c, int n, const double* tol, qcd_rhs_stats* st) {
       if (active[r] && h_rn2[r] != 0.0) psi_zero = false;
   }
   bool first_residual = true;
+  // D psi of the true residual in FP32 when every tolerance allows it
+  bool resid_f32 = prec == QCD_PREC_F32 && P.resid_f32_tol > 0;
+  for (int r = 0; r < n; r++)
+    if (tol[r] < P.resid_f32_tol) resid_f32 = false;
 
   for (;;) {
-    // true residual rho = eta - D psi (FP64)
+    // true residual rho = eta - D psi (FP64 difference and norm)
     QCD_TRY(upload_mask(active));
     int nact_now = 0;
     for (int r = 0; r < n; r++) nact_now += active[r];
     if (first_residual && psi_zero) {
       QCD_TRY(blas_convert(c, w.eta, QCD_PREC_F64, w.rho, QCD_PREC_F64, n, w.mask));
+    } else if (resid_f32) {
+      // sapin and delta are free between restart cycles
+      QCD_TRY(blas_convert(c, w.psi, QCD_PREC_F64, w.sapin, QCD_PREC_F32, n, w.mask));
+      QCD_TRY(dslash_apply(c, w.sapin, w.delta, QCD_PREC_F32, n, 0, w.mask, nact_now));
+      QCD_TRY(blas_convert(c, w.delta, QCD_PREC_F32, w.tmp, QCD_PREC_F64, n, w.mask));
+      QCD_TRY(blas_xmy(c, w.eta, w.tmp, w.rho, QCD_PREC_F64, n, w.mask));
     } else {
       QCD_TRY(dslash_apply(c, w.psi, w.tmp, QCD_PREC_F64, n, 0, w.mask, nact_now));
       QCD_TRY(blas_xmy(c, w.eta, w.tmp, w.rho, QCD_PREC_F64, n, w.mask));

@@ -47,7 +47,7 @@ class SolverParams(ctypes.Structure):
         ("max_outer", ctypes.c_int), ("restart_drop", ctypes.c_double), ("precision", ctypes.c_int),
         ("rhs_tile", ctypes.c_int), ("sap_half", ctypes.c_int), ("dfl", ctypes.c_int),
         ("dfl_little_iters", ctypes.c_int), ("dfl_gen_iters", ctypes.c_int), ("graphs", ctypes.c_int),
-        ("basis_half", ctypes.c_int),
+        ("basis_half", ctypes.c_int), ("resid_f32_tol", ctypes.c_double),
     ]
 
 

@@ -25,6 +25,7 @@ import pytest
 from gpu_util import (elem_err, elem_err_faces, make_lattice, oracle_solve_many, record, rel, timeslice_err, to_dev,
                       to_host)
 from paper_1605_00564_gb300 import synth
+from paper_1605_00564_gb300.qcd import QcdError
 
 pytestmark = pytest.mark.gpu
 
@@ -175,6 +176,34 @@ def test_solve_fp16_basis(small, tol):
     it32 = sum(s["outer_iters"] for s in st32)
     if tol >= 1e-3:
         assert it16 <= 1.2 * it32 + 12, (it16, it32)
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-10])
+def test_solve_fp32_true_residual(small, tol):
+    """resid_f32_tol = 1e-3: a tile whose tolerances are all >= 1e-3 takes its
+    true residuals from the FP32 operator; a tighter tile keeps FP64 ones (the
+    same bits as with the option off).  Every RHS meets its tolerance in the
+    oracle's FP64 residual, and the reported residual matches the oracle's to
+    far below the tolerance."""
+    lat, op, _ = small
+    lat.set_params(block=(4, 4, 4, 4), ncy=5, nmr=4, nkv=8, precision="f32", sap_half=1, dfl=0, basis_half=0)
+    src = synth.point_sources(lat.dims, (4, 0, 4, 0))
+    eta = to_dev(src)
+    try:
+        psi64, st64 = lat.solve(eta, tol)
+        lat.set_params(resid_f32_tol=1e-3)
+        psi, st = lat.solve(eta, tol)
+        with pytest.raises(QcdError):
+            lat.set_params(resid_f32_tol=1e-5)
+    finally:
+        lat.set_params(resid_f32_tol=0.0, nkv=16)
+    psi = to_host(psi)
+    for r in range(12):
+        res = np.linalg.norm(src[r] - op.D(psi[r])) / np.linalg.norm(src[r])
+        assert st[r]["status"] == "QCD_OK" and res <= 1.02 * tol, (r, res, st[r])
+        assert record("resid_f32_report_%g" % tol, abs(st[r]["true_rel_residual"] - res) / tol) < 1e-2, (r, res, st[r])
+    if tol < 1e-3:
+        assert np.array_equal(psi, to_host(psi64))
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 5e-6)])
