@@ -16,6 +16,7 @@ smaller lattice understate the full-size cost: the CPU figure is favourable
 to the CPU.)
 
     python -m oracle.gcr_iteration_counts        # writes oracle/gcr_iteration_counts.json
+    python -m oracle.gcr_iteration_counts --dims 24 12 12 12 --out <path>   # a smaller copy
 """
 from __future__ import annotations
 
@@ -36,7 +37,14 @@ CASE = dict(dims=(32, 16, 16, 16), eps=0.15, csw=1.9, kappa=0.1300, seed=1605005
 
 
 def main():
-    c = CASE
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs=4, default=None, help="T X Y Z (default: 32 16 16 16)")
+    ap.add_argument("--out", default=OUT)
+    args = ap.parse_args()
+    c = dict(CASE)
+    if args.dims:
+        c["dims"] = tuple(args.dims)
     U = synth.gauge_field(c["dims"], c["eps"], c["seed"])
     op = Operator(U, c["kappa"], c["csw"], c["bc_t"])
     eta = synth.point_source(c["dims"], c["src"], c["spin"], c["colour"])
@@ -45,11 +53,11 @@ def main():
     t1 = time.perf_counter()
     _, n_e, r_e = gcr(op, eta, tol=c["exact_tol"], nkv=c["nkv"], psi0=psi)
     t2 = time.perf_counter()
-    rec = dict(CASE)
+    rec = dict(c)
     rec.update(dict(iters_sloppy=int(n_s), residual_sloppy=float(r_s), iters_exact_from_sloppy=int(n_e),
                     residual_exact=float(r_e), seconds_sloppy=round(t1 - t0, 1), seconds_exact=round(t2 - t1, 1),
                     solver="oracle.solve.gcr (restarted GCR, nkv 24, FP64, unpreconditioned)"))
-    with open(OUT, "w") as f:
+    with open(args.out, "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))
 
