@@ -177,10 +177,10 @@ def oracle_sample(max_iter=8, parallel=True):
 
     Time per iteration of the oracle's unpreconditioned GCR (each iteration one
     application of its D plus the Gram-Schmidt; the solve's initial and restart
-    applications of D are charged to the sampled iterations) measured on a
-    16^3x32 field of the workload's distribution, scaled by each lattice's
-    volume; times the iteration counts of completed oracle solves on that
-    16^3x32 field (oracle/gcr_iteration_counts.json: to 1e-3, and to 1e-10 from
+    applications of D are charged to the sampled iterations) measured on the
+    field of the workload's distribution that oracle/gcr_iteration_counts.json
+    names, scaled by each lattice's volume; times the iteration counts of
+    completed oracle solves on that field (the same file: to 1e-3, and to 1e-10 from
     the 1e-3 solution, as the benchmark's exact solves start), for every
     lattice of the batch.  Measured in one process (numpy's own threads), and
     with one single-threaded process per host core working at once.  Returns
@@ -224,14 +224,15 @@ def oracle_sample(max_iter=8, parallel=True):
         # aggregate: cores solves in flight, each at its own per-iteration time
         t_iter_all = float(np.mean([w / it for w, _, it in res]))
         rate_all = cores * solves / (t_iter_all * vol_iters)
-    desc = ("oracle.solve.gcr (unpreconditioned restarted GCR, FP64 numpy): %d iterations timed on a 16^3x32 field "
+    lab = lattice_label(dims)
+    desc = ("oracle.solve.gcr (unpreconditioned restarted GCR, FP64 numpy): %d iterations timed on a %s field "
             "of the workload's distribution: %.3f s per iteration in one process (%d threads)%s; per lattice of the "
             "batch the time per iteration scaled by its volume; iteration counts of completed oracle solves on the "
-            "16^3x32 field: %d to %g, %d more to %g from there (oracle/gcr_iteration_counts.json, used for both "
+            "%s field: %d to %g, %d more to %g from there (oracle/gcr_iteration_counts.json, used for both "
             "lattices); value = %d solves / (sum over lattices of volume ratio x (96 x %d + 12 x %d) iterations)%s" % (
-                max_iter, t_iter1, threads1,
+                max_iter, lab, t_iter1, threads1,
                 (", %.3f s per iteration with %d single-threaded processes at once" % (t_iter_all, cores))
-                if parallel else "", n_s, WORKLOAD["sloppy_tol"], n_e, WORKLOAD["exact_tol"], solves, n_s, n_e,
+                if parallel else "", lab, n_s, WORKLOAD["sloppy_tol"], n_e, WORKLOAD["exact_tol"], solves, n_s, n_e,
                 (" x %d processes" % cores) if parallel else ""))
     return rate_all, desc, cores, rate1
 
@@ -572,7 +573,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-iters", type=int, default=8,
-                    help="oracle GCR iterations timed (on 16^3x32) for cpu_baseline")
+                    help="oracle GCR iterations timed (on the counts file's lattice) for cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=3,
                     help="oracle GCR iterations timed per step of --impl reference")
     ap.add_argument("--skip-cpu", action="store_true")
