@@ -13,12 +13,14 @@
 // Each FP32 operand x is split as x = hi + lo with hi = x truncated to the 19
 // bits the tensor core reads and lo = x - hi (exact), and the product is
 // hi*hi + hi*lo + lo*hi (error of order 2^-21 relative, the FP32 level of the
-// FP32 fields).  Each chunk's accumulator is read with tcgen05.ld and summed
-// in FP64; A is stored in FP64.
+// FP32 fields).  Each chunk's accumulator is read with tcgen05.ld and added to
+// a compensated FP32 sum (TwoSum, sum and error kept apart), widened to FP64
+// at the end; A is stored in FP64.
 //
 // One CTA of 128 threads per (block, 128-row tile); one elected thread issues
 // the MMAs and commits them to an mbarrier; all waits on it are bounded (on
 // timeout the kernel records an error, frees its tensor memory and returns).
+// The staged operands are double-buffered so that staging overlaps the MMAs.
 #include <stdint.h>
 
 #include "qcd_internal.cuh"
@@ -69,11 +71,6 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-__device__ inline Cplx<float> field_comp(const char* field, int V, int s, int comp) {
-  const float4 v = __ldg((const float4*)field + (size_t)(comp >> 1) * V + s);
-  return (comp & 1) ? cmk(v.z, v.w) : cmk(v.x, v.y);
-}
-
 struct TcGeom {
   int b[4], nb[4], vb;
 };
@@ -96,26 +93,50 @@ __device__ inline int tc_site(const TcGeom& bg, const Geom& g, int blk, int l, i
   return ((c[0] * g.L[3] + c[3]) * g.L[2] + c[2]) * g.L[1] + c[1];
 }
 
+// Stage the 12 spin-colour components of one site of one field as TF32 head
+// and remainder: x[q] holds components 2q, 2q + 1 (re, im, re, im); the real
+// parts go to row r_re, the imaginary parts to row r_im, at K entries
+// e0 .. e0 + 11.
+__device__ inline void stage_site(unsigned char* hi, unsigned char* lo, int r_re, int r_im, int e0,
+                                  const float4 (&x)[6]) {
+#pragma unroll
+  for (int c = 0; c < 2; c++) {
+    const int row = c ? r_im : r_re;
+#pragma unroll
+    for (int g = 0; g < 3; g++) {   // K entries e0 + 4 g .. e0 + 4 g + 3: components 4 g .. 4 g + 3
+      const float4 a = x[2 * g], b = x[2 * g + 1];
+      const float4 v = c ? make_float4(a.y, a.w, b.y, b.w) : make_float4(a.x, a.z, b.x, b.z);
+      const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+      const uint32_t off = stage_off(row, e0 + 4 * g);
+      *(float4*)(hi + off) = h;
+      *(float4*)(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    }
+  }
+}
+
 // CTA (block b, tile t): rows 128 t .. 128 t + 127 of the X side against all
 // N = 2 NSP columns of the Phi side.  The accumulator in tensor memory holds
 // one chunk (KC entries of K, 9 MMAs); after each chunk every thread adds its
-// row's N values to FP64 registers and the next chunk starts a fresh
+// row's N values to its compensated sums and the next chunk starts a fresh
 // accumulation, so no FP32 accumulator sums more than one chunk (the tensor
 // core's accumulation rounds toward zero by up to an FP32 ulp per MMA, which
 // over the whole K of a 4^4 block biased the sums by 5e-5 relative).
+// The operands are double-buffered: chunk ch + 1 is staged while the MMAs of
+// chunk ch run.  Staging works in tasks of one row pair (the real and the
+// imaginary row of one field) and one of the chunk's two sites: six 16-byte
+// loads of the site's components feed both rows.
 template <int NSP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_dfl_little_tc(const char* __restrict__ phi, const char* __restrict__ Y, double* __restrict__ A, Geom g,
                     TcGeom bg, int ns, int tmem_cols, int* __restrict__ err) {
   constexpr int N = 2 * NSP;           // real columns of the Phi side
   constexpr int M = 9 * 2 * NSP;       // real rows of the X side
+  constexpr size_t A_BYTES = 128 * KC * 4, B_BYTES = N * KC * 4;
+  constexpr size_t BUF = 2 * (A_BYTES + B_BYTES);   // hi and lo of both operands
+  constexpr int XTASKS = 64 * 2, TASKS = XTASKS + NSP * 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  unsigned char* a_hi = smem_raw;
-  unsigned char* a_lo = a_hi + 128 * KC * 4;
-  unsigned char* b_hi = a_lo + 128 * KC * 4;
-  unsigned char* b_lo = b_hi + N * KC * 4;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int blk = blockIdx.x, tile = blockIdx.y;
   const size_t fb = FieldsF::spinor_bytes * (size_t)g.V;
@@ -140,59 +161,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t bar = smem_u32(&mbar);
   bool ok = true;
   uint32_t phase = 0;
-  double acc[N];
+  // compensated FP32 sums of the chunks' results (sum + running error, TwoSum
+  // per chunk): FP64 additions run at 1/64 of the FP32 rate on this GPU
+  float sum[N], cmp[N];
 #pragma unroll
-  for (int q = 0; q < N; q++) acc[q] = 0.0;
+  for (int q = 0; q < N; q++) sum[q] = cmp[q] = 0.f;
+
+  // stage chunk ch (sites 2 ch, 2 ch + 1 of the block) into buffer buf
+  auto stage = [&](int ch, int buf) {
+    unsigned char* a_hi = smem_raw + buf * BUF;
+    unsigned char* a_lo = a_hi + A_BYTES;
+    unsigned char* b_hi = a_lo + A_BYTES;
+    unsigned char* b_lo = b_hi + B_BYTES;
+    for (int t = tid; t < TASKS; t += TC_THREADS) {
+      const int site = t & 1;
+      int lc[4];
+      const int s = tc_site(bg, g, blk, 2 * ch + site, lc);
+      float4 x[6];
+      bool on = false;
+      const char* src = nullptr;
+      int r0;
+      unsigned char *hi, *lo;
+      if (t < XTASKS) {
+        r0 = 2 * (t >> 1);                    // rows r0 (real part), r0 + 1 (imaginary part) of the tile
+        hi = a_hi;
+        lo = a_lo;
+        const int grow = tile * 128 + r0;
+        const int j = (grow >> 1) % NSP, p = (grow >> 1) / NSP;
+        if (grow < M && j < ns) {
+          int part = 0;
+          on = true;
+          if (p > 0) {
+            const int mu = (p - 1) >> 1;
+            // lc[mu], b[mu] by selects (no local-memory indexing)
+            const int lm = mu == 0 ? lc[0] : mu == 1 ? lc[1] : mu == 2 ? lc[2] : lc[3];
+            const int bm = mu == 0 ? bg.b[0] : mu == 1 ? bg.b[1] : mu == 2 ? bg.b[2] : bg.b[3];
+            on = ((p - 1) & 1) == 0 ? lm == bm - 1 : lm == 0;
+            part = 1 + mu;
+          }
+          src = Y + ((size_t)part * ns + j) * fb;
+        }
+      } else {
+        const int k = (t - XTASKS) >> 1;      // Phi rows k (real part) and NSP + k (imaginary part)
+        r0 = k;
+        hi = b_hi;
+        lo = b_lo;
+        on = k < ns;
+        src = phi + (size_t)k * fb;
+      }
+#pragma unroll
+      for (int q = 0; q < 6; q++)
+        x[q] = on ? __ldg((const float4*)src + (size_t)q * g.V + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+      // X side: real and imaginary rows neighbours; Phi side: NSP apart
+      if (t < XTASKS)
+        stage_site(hi, lo, r0, r0 + 1, 12 * site, x);
+      else
+        stage_site(hi, lo, r0, r0 + NSP, 12 * site, x);
+    }
+  };
 
   const int nchunks = bg.vb * 12 / KC;
+  stage(0, 0);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
   for (int ch = 0; ch < nchunks && ok; ch++) {
-    // stage the chunk: K entries e = 0..KC-1 are (site l = (ch*KC + e) / 12, comp = (ch*KC + e) % 12)
-    for (int idx = tid; idx < (128 + N) * KC; idx += TC_THREADS) {
-      const bool xside = idx < 128 * KC;
-      const int row = xside ? idx / KC : (idx - 128 * KC) / KC;
-      const int e = idx % KC;
-      const int kk = ch * KC + e;
-      const int l = kk / 12, comp = kk % 12;
-      int lc[4];
-      const int s = tc_site(bg, g, blk, l, lc);
-      float v = 0.f;
-      if (xside) {
-        const int grow = tile * 128 + row;
-        if (grow < M) {
-          const int c = grow & 1, j = (grow >> 1) % NSP, p = (grow >> 1) / NSP;
-          if (j < ns) {
-            bool on = true;
-            int part = 0;
-            if (p > 0) {
-              const int mu = (p - 1) >> 1;
-              on = ((p - 1) & 1) == 0 ? lc[mu] == bg.b[mu] - 1 : lc[mu] == 0;
-              part = 1 + mu;
-            }
-            if (on) {
-              const Cplx<float> z = field_comp(Y + ((size_t)part * ns + j) * fb, g.V, s, comp);
-              v = c ? z.im : z.re;
-            }
-          }
-        }
-        const float hi = tf32_hi(v);
-        *(float*)(a_hi + stage_off(row, e)) = hi;
-        *(float*)(a_lo + stage_off(row, e)) = v - hi;
-      } else {
-        const int c = row / NSP, k = row % NSP;
-        if (k < ns) {
-          const Cplx<float> z = field_comp(phi + (size_t)k * fb, g.V, s, comp);
-          v = c ? z.im : z.re;
-        }
-        const float hi = tf32_hi(v);
-        *(float*)(b_hi + stage_off(row, e)) = hi;
-        *(float*)(b_lo + stage_off(row, e)) = v - hi;
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    const int buf = ch & 1;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned char* a_hi = smem_raw + buf * BUF;
+      const unsigned char* a_lo = a_hi + A_BYTES;
+      const unsigned char* b_hi = a_lo + A_BYTES;
+      const unsigned char* b_lo = b_hi + B_BYTES;
       for (int ks = 0; ks < KC / 8; ks++)
         for (int term = 0; term < 3; term++) {
           const unsigned char* aop = term == 2 ? a_lo : a_hi;
@@ -209,14 +249,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                    : "memory");
     }
-    // the MMAs of this chunk complete before its staged operands are
-    // overwritten and before the accumulator is read
-    if (!mbar_wait(bar, phase)) {
-      ok = false;
-      if (tid == 0) atomicExch(err, 1);
-    }
+    // the next chunk goes into the other buffer, whose MMAs completed in the
+    // previous iteration, while this chunk's MMAs run
+    if (ch + 1 < nchunks) stage(ch + 1, buf ^ 1);
+    // this chunk's MMAs complete before the accumulator is read and before
+    // their buffer is staged again
+    const bool done = mbar_wait(bar, phase);
     phase ^= 1u;
-    if (ok) {
+    if (done) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int cb = 0; cb < N; cb += 16) {
@@ -230,23 +270,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 16; q++) acc[cb + q] += (double)__uint_as_float(r[q]);
+        for (int q = 0; q < 16; q++) {
+          const float x = __uint_as_float(r[q]), a = sum[cb + q];
+          const float t = a + x, bp = t - a;
+          cmp[cb + q] += (a - (t - bp)) + (x - bp);   // the rounding error of a + x, exactly
+          sum[cb + q] = t;
+        }
       }
     }
+    // the staged writes of the next chunk are visible to the tensor core and
+    // the accumulator reads are done before the next MMAs; every thread leaves
+    // the loop together if any wait gave up
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    ok = __syncthreads_and(done) != 0;
   }
-  if (!ok) mbar_wait(bar, phase ^ 1u);   // a last bounded wait for MMAs still in flight
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(bar, phase ^ 1u);   // a last bounded wait for MMAs still in flight
+  }
 
   if (ok) {
     // rows (p, j, R) and (p, j, S) are neighbouring lanes: Re A = D[R][k] + D[S][NSP + k],
-    // Im A = D[S][k] - D[R][NSP + k]
+    // Im A = D[S][k] - D[R][NSP + k]; sum and error widened to FP64 once
     const int row = tile * 128 + 32 * warp + lane;
     const int c = row & 1, j = (row >> 1) % NSP, p = (row >> 1) / NSP;
 #pragma unroll
     for (int k = 0; k < NSP; k++) {
-      const double other = __shfl_xor_sync(0xffffffffu, acc[NSP + k], 1);
-      const double v = c == 0 ? acc[k] + other : acc[k] - other;
+      const double mine = (double)sum[k] + (double)cmp[k];
+      const double other = __shfl_xor_sync(0xffffffffu, (double)sum[NSP + k] + (double)cmp[NSP + k], 1);
+      const double v = c == 0 ? mine + other : mine - other;
       if (p < 9 && j < ns && k < ns) A[((((size_t)blk * 9 + p) * ns + k) * ns + j) * 2 + c] = v;
     }
   }
@@ -280,7 +333,7 @@ qcd_status dfl_little_tc(qcd_ctx* c, const void* phi, const void* Y, double* A, 
   const int ntiles = (M + 127) / 128;
   const int cols = N < 32 ? 32 : N;                              // N is 16, 32, 48 or 64
   const int tmem_cols = cols == 48 ? 64 : cols;                  // a power of two >= 32
-  const size_t smem = (size_t)(128 + N) * KC * 4 * 2;
+  const size_t smem = (size_t)(128 + N) * KC * 4 * 2 * 2;   // hi + lo, double-buffered
   const dim3 grid((unsigned)nblk, (unsigned)ntiles);
   ProfScope ps(c, FAM_DFL, (double)spinor_bytes(c, QCD_PREC_F32) * ns * 6,
                2.0 * nblk * (double)M * N * bg.vb * 12 * 3);
