@@ -279,17 +279,37 @@ struct RStore<true> {
     return cmk(f.x, f.y);
   }
 };
+// FP32: 16-byte records, word q of site l at ((float4*)r_s)[q * vb + l] holding
+// components 2q and 2q + 1 (one 128-bit load per two components); bf16: one
+// 4-byte word per component at r_s[k * vb + l]
 template <bool BF>
 __device__ inline Spinor<float> rs_load(const typename RStore<BF>::T* r_s, int vb, int l) {
   Spinor<float> o;
+  if (BF) {
 #pragma unroll
-  for (int k = 0; k < 12; k++) o.c[k] = RStore<BF>::get(r_s[k * vb + l]);
+    for (int k = 0; k < 12; k++) o.c[k] = RStore<BF>::get(r_s[k * vb + l]);
+  } else {
+    const float4* w = reinterpret_cast<const float4*>(r_s);
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      const float4 v = w[q * vb + l];
+      o.c[2 * q] = cmk(v.x, v.y);
+      o.c[2 * q + 1] = cmk(v.z, v.w);
+    }
+  }
   return o;
 }
 template <bool BF>
 __device__ inline void rs_store(typename RStore<BF>::T* r_s, int vb, int l, const Spinor<float>& v) {
+  if (BF) {
 #pragma unroll
-  for (int k = 0; k < 12; k++) r_s[k * vb + l] = RStore<BF>::put(v.c[k]);
+    for (int k = 0; k < 12; k++) r_s[k * vb + l] = RStore<BF>::put(v.c[k]);
+  } else {
+    float4* w = reinterpret_cast<float4*>(r_s);
+#pragma unroll
+    for (int q = 0; q < 6; q++)
+      w[q * vb + l] = make_float4(v.c[2 * q].re, v.c[2 * q].im, v.c[2 * q + 1].re, v.c[2 * q + 1].im);
+  }
 }
 
 // the full 3x3 link (staged with its third row already reconstructed)
