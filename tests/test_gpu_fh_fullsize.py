@@ -34,7 +34,7 @@ def _grads(lat, U, src, w):
     C = nucleon_fh(m, lam, lat, U, CSW, src, TOL)
     L = (torch.from_numpy(w) * C[0, :, 0]).sum()
     L.backward()
-    return float(L), m.grad.item(), lam.grad.item()
+    return float(L.detach()), m.grad.item(), lam.grad.item()
 
 
 def test_fh_gradients_24c48():
