@@ -6,6 +6,7 @@ L2 where DRAM figures matter).
     python -m paper_1605_00564_gb300.cases dslash12    # FP32 Dslash, 32^3x64, 12 RHS, 3 launches
     python -m paper_1605_00564_gb300.cases sap         # SAP sweeps, 16^3x32, 12 RHS, FP16 block copies
     python -m paper_1605_00564_gb300.cases sap32       # same with FP32 block copies
+    python -m paper_1605_00564_gb300.cases sap_32c64   # SAP sweeps at 32^3x64, 12 RHS (DRAM counters only)
     python -m paper_1605_00564_gb300.cases deflation   # deflation setup + one deflated sloppy solve, 16^3x32
     python -m paper_1605_00564_gb300.cases contract    # nucleon contraction, 16^3x32
     python -m paper_1605_00564_gb300.cases gcr         # sloppy SAP-GCR solve, 16^3x32, 12 RHS, nkv 8, FP16 chi_k
@@ -44,6 +45,15 @@ def sap(half=1):
         lat.apply_sap(psi)
 
 
+def sap_32c64():
+    import torch
+    lat = _lattice((64, 32, 32, 32), kappa=0.13)
+    psi = torch.randn(lat.spinor_shape(12), dtype=torch.complex128, device="cuda")
+    lat.set_params(block=(4, 4, 4, 4), ncy=1, nmr=4, sap_half=1)
+    for _ in range(2):
+        lat.apply_sap(psi)
+
+
 def deflation():
     import torch
     from paper_1605_00564_gb300 import synth
@@ -71,8 +81,8 @@ def gcr(basis_half=1):
     lat.solve(eta, 1e-3)
 
 
-CASES = {"dslash": dslash, "dslash12": lambda: dslash(12), "sap": sap, "sap32": lambda: sap(0), "deflation": deflation, "contract": contract,
-         "gcr": gcr, "gcr32": lambda: gcr(0)}
+CASES = {"dslash": dslash, "dslash12": lambda: dslash(12), "sap": sap, "sap32": lambda: sap(0), "sap_32c64": sap_32c64,
+         "deflation": deflation, "contract": contract, "gcr": gcr, "gcr32": lambda: gcr(0)}
 
 if __name__ == "__main__":
     import torch
