@@ -3,17 +3,19 @@ field distribution, for the CPU baseline of bench.py.
 
 Test infrastructure only (see ``oracle/__init__``).
 
-The benchmark solves point sources on 32^3x64 (U = exp(0.15 i H), c_sw 1.9,
-kappa 0.1300) to 1e-3 and, for the bias correction, to 1e-10 starting from
-the 1e-3 solution (Sec. 2.1, eqs. caa1/caa2).  A complete unpreconditioned
-oracle solve at that size does not finish in reasonable time on host cores,
-so this script completes the same solves on a 16^3x32 field drawn from the
-same distribution (same eps, c_sw, kappa; its own seed) and records the
-iteration counts; bench.py multiplies them by the time per oracle GCR
-iteration measured at 32^3x64.  (The count of an unpreconditioned solver
-grows with the volume as the lowest modes move down, so counts taken on the
-smaller lattice understate the full-size cost: the CPU figure is favourable
-to the CPU.)
+The benchmark solves point sources on 32^3x64 and 24^3x48 (U = exp(0.15 i H),
+c_sw 1.9, kappa 0.1300) to 1e-3 and, for the bias correction, to 1e-10
+starting from the 1e-3 solution (Sec. 2.1, eqs. caa1/caa2).  A complete
+unpreconditioned oracle solve at those sizes does not finish in reasonable
+time on host cores, so this script completes the same solves on a smaller
+field drawn from the same distribution (same eps, c_sw, kappa; its own seed)
+and records the iteration counts; bench.py multiplies them by the time per
+oracle GCR iteration measured on that field and scaled by volume.  (The count
+of an unpreconditioned solver grows with the volume as the lowest modes move
+down, so counts taken on the smaller lattice understate the full-size cost:
+the CPU figure is favourable to the CPU.)  The committed file was written
+with --dims 16 8 8 8: on 16^3x32 the exact solve had not finished after
+several hours on the build machine's cores.
 
     python -m oracle.gcr_iteration_counts        # writes oracle/gcr_iteration_counts.json
     python -m oracle.gcr_iteration_counts --dims 24 12 12 12 --out <path>   # a smaller copy
