@@ -346,15 +346,39 @@ __global__ void k_dfl_block_inverse(const double2* __restrict__ A, double2* __re
 }
 
 // ---------------------------------------------------------------------------
-// Little operator and little vector algebra.  x, y: float2 [nrhs][nblk][ns];
-// A and the diagonal-block inverses are FP64, the products are summed in FP64.
+// Little operator and little vector algebra.  x, y: float2 [nrhs][nblk][ns].
+// A and the diagonal-block inverses are stored in FP64; the little solve
+// applies FP32 copies of them (an approximate inverse inside the flexible
+// preconditioner, whose FP32 vectors bound its accuracy anyway: FP64
+// arithmetic runs at 1/64 of the FP32 rate on this GPU).  The FP64 form
+// serves the exact products A x of the test entry point.
 // ---------------------------------------------------------------------------
-// y = A x (nparts = 9) or y = Ainv x (nparts = 1, diagonal blocks only)
-__global__ void k_little_apply(const double2* __restrict__ M, int nparts, const float2* __restrict__ x,
+__device__ inline void little_mac(double& ar, double& ai, double2 a, float2 v) {
+  ar = fma(a.x, (double)v.x, ar);
+  ar = fma(-a.y, (double)v.y, ar);
+  ai = fma(a.x, (double)v.y, ai);
+  ai = fma(a.y, (double)v.x, ai);
+}
+__device__ inline void little_mac(float& ar, float& ai, float2 a, float2 v) {
+  ar = fmaf(a.x, v.x, ar);
+  ar = fmaf(-a.y, v.y, ar);
+  ai = fmaf(a.x, v.y, ai);
+  ai = fmaf(a.y, v.x, ai);
+}
+
+// y = A x (nparts = 9) or y = Ainv x (nparts = 1, diagonal blocks only).  One
+// CTA per block, thread (k, rr) = row k for the RHS rr, rr + rb, ...: the rb
+// threads of a row read the same matrix row (L1 broadcast), the ns threads of
+// an RHS the same neighbour vector.  MT = double2: FP64 products and sums;
+// float2: FP32.
+template <typename MT>
+__global__ void k_little_apply(const MT* __restrict__ M, int nparts, const float2* __restrict__ x,
                                float2* __restrict__ y, BlkGeom bg, int ns, int nrhs, const int* mask) {
+  using RT = decltype(MT::x);
   const int blk = blockIdx.x;
-  const int k = threadIdx.x;   // row
-  if (k >= ns) return;
+  const int k = threadIdx.x % ns, rr = threadIdx.x / ns;
+  const int rb = blockDim.x / ns;
+  if (rr >= rb) return;
   int bc[4];
   blk_coords(bg, blk, bc);
   int nbr[9];
@@ -366,21 +390,22 @@ __global__ void k_little_apply(const double2* __restrict__ M, int nparts, const 
     cc[mu] = (bc[mu] - 1 + bg.nb[mu]) % bg.nb[mu];
     nbr[2 + 2 * mu] = blk_index(bg, cc);
   }
-  for (int r = 0; r < nrhs; r++) {
+  for (int r = rr; r < nrhs; r += rb) {
     if (mask && !mask[r]) continue;
-    double ar = 0, ai = 0;
+    RT ar = 0, ai = 0;
     for (int p = 0; p < nparts; p++) {
-      const double2* row = M + (((size_t)blk * nparts + p) * ns + k) * ns;
+      const MT* row = M + (((size_t)blk * nparts + p) * ns + k) * ns;
       const float2* xv = x + ((size_t)r * bg.nblk + nbr[p]) * ns;
-      for (int l = 0; l < ns; l++) {
-        const double2 a = __ldg(row + l);
-        const float2 v = xv[l];
-        ar += a.x * v.x - a.y * v.y;
-        ai += a.x * v.y + a.y * v.x;
-      }
+      for (int l = 0; l < ns; l++) little_mac(ar, ai, __ldg(row + l), __ldg(xv + l));
     }
     y[((size_t)r * bg.nblk + blk) * ns + k] = make_float2((float)ar, (float)ai);
   }
+}
+
+// FP32 copy of an FP64 complex array
+__global__ void k_to_float2(const double2* __restrict__ in, float2* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
 // per-rhs dots d[j][r] = (q_j, v) for j < nj (q_j at qbase + j*stride), FP64 partials
@@ -479,7 +504,7 @@ __global__ void k_little_update(float2* __restrict__ x, float2* __restrict__ res
 struct DflState {
   int ns = 0, ready = 0;
   BlkGeom bg;
-  DevBuf phi, A, Ainv, Y, little, part, tmp, flags;
+  DevBuf phi, A, Ainv, Af, Ainvf, Y, little, part, tmp, flags;
 };
 
 static DflState* dfl_of(qcd_ctx* c) {
@@ -493,6 +518,8 @@ void dfl_free(qcd_ctx* c) {
   devbuf_free(d->phi);
   devbuf_free(d->A);
   devbuf_free(d->Ainv);
+  devbuf_free(d->Af);
+  devbuf_free(d->Ainvf);
   devbuf_free(d->Y);
   devbuf_free(d->little);
   devbuf_free(d->part);
@@ -549,7 +576,57 @@ static qcd_status dfl_little_build(qcd_ctx* c) {
       return QCD_ERR_BREAKDOWN;
     }
   }
+  {
+    // FP32 copies for the little solve
+    const size_t na = (size_t)bg.nblk * 9 * ns * ns, ni = (size_t)bg.nblk * ns * ns;
+    QCD_TRY(devbuf_ensure(d->Af, sizeof(float2) * na));
+    QCD_TRY(devbuf_ensure(d->Ainvf, sizeof(float2) * ni));
+    ProfScope ps(c, FAM_DFL, 24.0 * (na + ni), 0.0, 2);
+    k_to_float2<<<1024, 256, 0, c->stream>>>((const double2*)d->A.p, (float2*)d->Af.p, na);
+    k_to_float2<<<1024, 256, 0, c->stream>>>((const double2*)d->Ainv.p, (float2*)d->Ainvf.p, ni);
+    QCD_CUDA_OK(cudaGetLastError());
+  }
   return QCD_OK;
+}
+
+// threads of a k_little_apply CTA: ns rows x rb RHS lanes, at most 256
+static int little_threads(int ns, int n) {
+  int rb = 256 / ns;
+  if (rb > n) rb = n;
+  if (rb < 1) rb = 1;
+  return ns * rb;
+}
+
+// m steps of block-Jacobi preconditioned GCR on the little vectors from x = 0:
+// res holds the right-hand side on entry and the residual on exit, xl the
+// approximate solution; P, Q: m (p, q) pairs of vlen float2 each.
+static void little_gcr(qcd_ctx* c, DflState* d, float2* res, float2* xl, float2* P, float2* Q, double2* part,
+                       double2* dots, int n, int m, const int* mask) {
+  const BlkGeom& bg = d->bg;
+  const int ns = d->ns;
+  const int N = bg.nblk * ns;
+  const size_t vlen = (size_t)N * n;
+  const int G = 64;
+  const dim3 gv(G, n);
+  const int nt = little_threads(ns, n);
+  cudaMemsetAsync(xl, 0, sizeof(float2) * vlen, c->stream);
+  for (int i = 0; i < m; i++) {
+    float2* pi = P + vlen * i;
+    float2* qi = Q + vlen * i;
+    k_little_apply<float2><<<bg.nblk, nt, 0, c->stream>>>((const float2*)d->Ainvf.p, 1, res, pi, bg, ns, n, mask);
+    k_little_apply<float2><<<bg.nblk, nt, 0, c->stream>>>((const float2*)d->Af.p, 9, pi, qi, bg, ns, n, mask);
+    if (i > 0) {
+      k_little_dots<<<gv, 256, 0, c->stream>>>(Q, vlen, i, qi, N, part, mask);
+      k_little_sum<<<dim3(i, n), 256, 0, c->stream>>>(part, i, G, dots, n, mask);
+      k_little_orth<<<gv, 256, 0, c->stream>>>(qi, pi, Q, P, vlen, i, dots, N, n, mask);
+    }
+    k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, qi, N, part, mask);
+    k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, mask);
+    k_little_scale2<<<gv, 256, 0, c->stream>>>(qi, pi, dots, N, mask);
+    k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, res, N, part, mask);
+    k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, mask);
+    k_little_update<<<gv, 256, 0, c->stream>>>(xl, res, pi, qi, dots, N, mask);
+  }
 }
 
 static qcd_status dfl_gs(qcd_ctx* c) {
@@ -657,25 +734,7 @@ qcd_status dfl_low_mode(qcd_ctx* c, const void* rho, void* x, int n, const int* 
   {
     ProfScope ps(c, FAM_DFL, 8.0 * vlen * (6.0 + 3.0 * m) * m, 0.0, 4 + 8 * m);
     QCD_CUDA_OK(cudaMemcpyAsync(res, cl, sizeof(float2) * vlen, cudaMemcpyDeviceToDevice, c->stream));
-    QCD_CUDA_OK(cudaMemsetAsync(xl, 0, sizeof(float2) * vlen, c->stream));
-    const dim3 gv(G, n);
-    for (int i = 0; i < m; i++) {
-      float2* pi = P + vlen * i;
-      float2* qi = Q + vlen * i;
-      k_little_apply<<<bg.nblk, ns, 0, c->stream>>>((const double2*)d->Ainv.p, 1, res, pi, bg, ns, n, mask);
-      k_little_apply<<<bg.nblk, ns, 0, c->stream>>>((const double2*)d->A.p, 9, pi, qi, bg, ns, n, mask);
-      if (i > 0) {
-        k_little_dots<<<gv, 256, 0, c->stream>>>(Q, vlen, i, qi, N, part, mask);
-        k_little_sum<<<dim3(i, n), 256, 0, c->stream>>>(part, i, G, dots, n, mask);
-        k_little_orth<<<gv, 256, 0, c->stream>>>(qi, pi, Q, P, vlen, i, dots, N, n, mask);
-      }
-      k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, qi, N, part, mask);
-      k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, mask);
-      k_little_scale2<<<gv, 256, 0, c->stream>>>(qi, pi, dots, N, mask);
-      k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, res, N, part, mask);
-      k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, mask);
-      k_little_update<<<gv, 256, 0, c->stream>>>(xl, res, pi, qi, dots, N, mask);
-    }
+    little_gcr(c, d, res, xl, P, Q, part, dots, n, m, mask);
     QCD_CUDA_OK(cudaGetLastError());
   }
   {
@@ -701,7 +760,8 @@ qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int
   float2* y = x + vlen;
   QCD_CUDA_OK(cudaMemcpyAsync(x, h.data(), sizeof(float2) * vlen, cudaMemcpyHostToDevice, c->stream));
   if (mode == 0) {
-    k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const double2*)d->A.p, 9, x, y, d->bg, d->ns, n, nullptr);
+    k_little_apply<double2><<<d->bg.nblk, little_threads(d->ns, n), 0, c->stream>>>((const double2*)d->A.p, 9, x, y,
+                                                                                    d->bg, d->ns, n, nullptr);
   } else {
     // reuse the solver on little vectors: the projection is skipped by copying x into the rhs slot
     QCD_TRY(devbuf_ensure(d->little, sizeof(float2) * vlen * (3 + 2 * (size_t)m)));
@@ -714,25 +774,7 @@ qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int
     double2* part = (double2*)d->part.p;
     double2* dots = part + (size_t)n * (m + 2) * G;
     QCD_CUDA_OK(cudaMemcpyAsync(res, x, sizeof(float2) * vlen, cudaMemcpyDeviceToDevice, c->stream));
-    QCD_CUDA_OK(cudaMemsetAsync(xl, 0, sizeof(float2) * vlen, c->stream));
-    const dim3 gv(G, n);
-    for (int i = 0; i < m; i++) {
-      float2* pi = P + vlen * i;
-      float2* qi = Q + vlen * i;
-      k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const double2*)d->Ainv.p, 1, res, pi, d->bg, d->ns, n, nullptr);
-      k_little_apply<<<d->bg.nblk, d->ns, 0, c->stream>>>((const double2*)d->A.p, 9, pi, qi, d->bg, d->ns, n, nullptr);
-      if (i > 0) {
-        k_little_dots<<<gv, 256, 0, c->stream>>>(Q, vlen, i, qi, N, part, nullptr);
-        k_little_sum<<<dim3(i, n), 256, 0, c->stream>>>(part, i, G, dots, n, nullptr);
-        k_little_orth<<<gv, 256, 0, c->stream>>>(qi, pi, Q, P, vlen, i, dots, N, n, nullptr);
-      }
-      k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, qi, N, part, nullptr);
-      k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, nullptr);
-      k_little_scale2<<<gv, 256, 0, c->stream>>>(qi, pi, dots, N, nullptr);
-      k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, res, N, part, nullptr);
-      k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, nullptr);
-      k_little_update<<<gv, 256, 0, c->stream>>>(xl, res, pi, qi, dots, N, nullptr);
-    }
+    little_gcr(c, d, res, xl, P, Q, part, dots, n, m, nullptr);
     QCD_CUDA_OK(cudaMemcpyAsync(y, xl, sizeof(float2) * vlen, cudaMemcpyDeviceToDevice, c->stream));
   }
   QCD_CUDA_OK(cudaGetLastError());
