@@ -408,24 +408,27 @@ __global__ void k_to_float2(const double2* __restrict__ in, float2* __restrict__
     out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
-// per-rhs dots d[j][r] = (q_j, v) for j < nj (q_j at qbase + j*stride), FP64 partials
+// per-rhs dots d[j][r] = (q_j, v) for j < nj (q_j at qbase + j*stride): CTA
+// (g, j, r) sums chunk g of the product of q_j and v for RHS r into part
+// [r][j][g].  Products and the per-thread sums in FP32 (the vectors are FP32),
+// widened to FP64 once per thread for the sum across threads.
 __global__ void k_little_dots(const float2* __restrict__ qbase, size_t stride, int nj, const float2* __restrict__ v,
                               int n, double2* __restrict__ part, const int* mask) {
   __shared__ double2 sh[32];
-  const int r = blockIdx.y;
+  const int g = blockIdx.x, j = blockIdx.y, r = blockIdx.z;
   if (mask && !mask[r]) return;
-  for (int j = 0; j < nj; j++) {
-    double2 acc = make_double2(0, 0);
-    const float2* q = qbase + j * stride + (size_t)r * n;
-    const float2* vv = v + (size_t)r * n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      float2 a = q[i], b = vv[i];
-      acc.x += (double)a.x * b.x + (double)a.y * b.y;
-      acc.y += (double)a.x * b.y - (double)a.y * b.x;
-    }
-    double2 t = cta_sum2(acc, sh);
-    if (threadIdx.x == 0) part[((size_t)r * nj + j) * gridDim.x + blockIdx.x] = t;
+  const float2* q = qbase + j * stride + (size_t)r * n;
+  const float2* vv = v + (size_t)r * n;
+  float ar = 0.f, ai = 0.f;
+  for (int i = g * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 a = q[i], b = vv[i];
+    ar = fmaf(a.x, b.x, ar);
+    ar = fmaf(a.y, b.y, ar);
+    ai = fmaf(a.x, b.y, ai);
+    ai = fmaf(-a.y, b.x, ai);
   }
+  const double2 t = cta_sum2(make_double2(ar, ai), sh);
+  if (threadIdx.x == 0) part[((size_t)r * nj + j) * gridDim.x + g] = t;
 }
 
 __global__ void k_little_sum(const double2* __restrict__ part, int nj, int G, double2* __restrict__ out, int nrhs,
@@ -608,6 +611,8 @@ static void little_gcr(qcd_ctx* c, DflState* d, float2* res, float2* xl, float2*
   const size_t vlen = (size_t)N * n;
   const int G = 64;
   const dim3 gv(G, n);
+  // dot chunks of about 8 elements per thread (at most G)
+  const int Gd = (N + 2047) / 2048 < G ? (N + 2047) / 2048 : G;
   const int nt = little_threads(ns, n);
   cudaMemsetAsync(xl, 0, sizeof(float2) * vlen, c->stream);
   for (int i = 0; i < m; i++) {
@@ -616,15 +621,15 @@ static void little_gcr(qcd_ctx* c, DflState* d, float2* res, float2* xl, float2*
     k_little_apply<float2><<<bg.nblk, nt, 0, c->stream>>>((const float2*)d->Ainvf.p, 1, res, pi, bg, ns, n, mask);
     k_little_apply<float2><<<bg.nblk, nt, 0, c->stream>>>((const float2*)d->Af.p, 9, pi, qi, bg, ns, n, mask);
     if (i > 0) {
-      k_little_dots<<<gv, 256, 0, c->stream>>>(Q, vlen, i, qi, N, part, mask);
-      k_little_sum<<<dim3(i, n), 256, 0, c->stream>>>(part, i, G, dots, n, mask);
+      k_little_dots<<<dim3(Gd, i, n), 256, 0, c->stream>>>(Q, vlen, i, qi, N, part, mask);
+      k_little_sum<<<dim3(i, n), 256, 0, c->stream>>>(part, i, Gd, dots, n, mask);
       k_little_orth<<<gv, 256, 0, c->stream>>>(qi, pi, Q, P, vlen, i, dots, N, n, mask);
     }
-    k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, qi, N, part, mask);
-    k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, mask);
+    k_little_dots<<<dim3(Gd, 1, n), 256, 0, c->stream>>>(qi, 0, 1, qi, N, part, mask);
+    k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, Gd, dots, n, mask);
     k_little_scale2<<<gv, 256, 0, c->stream>>>(qi, pi, dots, N, mask);
-    k_little_dots<<<gv, 256, 0, c->stream>>>(qi, 0, 1, res, N, part, mask);
-    k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, G, dots, n, mask);
+    k_little_dots<<<dim3(Gd, 1, n), 256, 0, c->stream>>>(qi, 0, 1, res, N, part, mask);
+    k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, Gd, dots, n, mask);
     k_little_update<<<gv, 256, 0, c->stream>>>(xl, res, pi, qi, dots, N, mask);
   }
 }
