@@ -197,46 +197,57 @@ __device__ inline Cplx<float> ld_comp(const char* field, int V, int s, int comp)
   return (comp & 1) ? cmk(v.z, v.w) : cmk(v.x, v.y);
 }
 
-// Projection c[r][b][k] = (phi_k^b, rho_r) for the unmasked right-hand sides
+// Projection c[r][b][k] = (phi_k^b, rho_r) for the unmasked right-hand sides.
+// One CTA per block, tiles of TS sites: staging tasks of one field (phi_k or
+// rho_r) at one site, six 16-byte loads for its 12 components, stored entry-
+// major (Pt[e][k], Rt[e][r], e = site * 12 + component) so that the threads of
+// one RHS read consecutive words of Pt and one broadcast word of Rt.
 __global__ void __launch_bounds__(GEMM_TPB) k_dfl_project(const char* __restrict__ phi, const char* __restrict__ rho,
                                                            float2* __restrict__ cout, Geom g, BlkGeom bg, int ns,
                                                            int nrhs, const int* mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cplx<float>* Pt = (Cplx<float>*)smem_raw;     // [ns][12][TS]
-  Cplx<float>* Rt = Pt + (size_t)ns * 12 * TS;   // [nrhs][12][TS]
+  float2* Pt = (float2*)smem_raw;                // [12 TS][ns]
+  float2* Rt = Pt + (size_t)12 * TS * ns;        // [12 TS][nrhs]
   const int blk = blockIdx.x;
   const size_t fb = FieldsF::spinor_bytes * (size_t)g.V;
   const int nout = ns * nrhs;
+  const int nf = ns + nrhs;
   Cplx<float> acc[4];
   for (int o = 0; o < 4; o++) acc[o] = cmk(0.f, 0.f);
   for (int t0 = 0; t0 < bg.vb; t0 += TS) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < (ns + nrhs) * 12 * TS; idx += blockDim.x) {
-      int i = idx % TS, comp = (idx / TS) % 12, k = idx / (12 * TS);
+    for (int task = threadIdx.x; task < nf * TS; task += blockDim.x) {
+      const int i = task % TS, f = task / TS;
       int lc[4], c[4];
-      int s = blk_site(bg, g, blk, t0 + i, lc, c);
-      if (k < ns) {
-        Pt[idx] = ld_comp(phi + k * fb, g.V, s, comp);
-      } else {
-        int r = k - ns;
-        Rt[(size_t)r * 12 * TS + (idx % (12 * TS))] =
-            (mask && !mask[r]) ? cmk(0.f, 0.f) : ld_comp(rho + r * fb, g.V, s, comp);
+      const int s = blk_site(bg, g, blk, t0 + i, lc, c);
+      const bool isphi = f < ns;
+      const int r = f - ns;
+      const bool on = isphi || !mask || mask[r];
+      const float4* src = (const float4*)(isphi ? phi + (size_t)f * fb : rho + (size_t)r * fb);
+      float2* dst = isphi ? Pt + f : Rt + r;
+      const int st = isphi ? ns : nrhs;
+#pragma unroll
+      for (int q = 0; q < 6; q++) {
+        const float4 v = on ? __ldg(src + (size_t)q * g.V + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+        dst[(size_t)(i * 12 + 2 * q) * st] = make_float2(v.x, v.y);
+        dst[(size_t)(i * 12 + 2 * q + 1) * st] = make_float2(v.z, v.w);
       }
     }
     __syncthreads();
     for (int o = 0; o < 4; o++) {
-      int idx = threadIdx.x + o * GEMM_TPB;
+      const int idx = threadIdx.x + o * GEMM_TPB;
       if (idx >= nout) break;
-      int r = idx / ns, k = idx - r * ns;
-      const Cplx<float>* pk = Pt + (size_t)k * 12 * TS;
-      const Cplx<float>* rr = Rt + (size_t)r * 12 * TS;
-      for (int e = 0; e < 12 * TS; e++) acc[o] = acc[o] + cdot(pk[e], rr[e]);
+      const int r = idx / ns, k = idx - r * ns;
+      for (int e = 0; e < 12 * TS; e++) {
+        const float2 a = Pt[(size_t)e * ns + k], b = Rt[(size_t)e * nrhs + r];
+        cmac_conj(acc[o], cmk(a.x, a.y), cmk(b.x, b.y));
+      }
     }
   }
   for (int o = 0; o < 4; o++) {
-    int idx = threadIdx.x + o * GEMM_TPB;
+    const int idx = threadIdx.x + o * GEMM_TPB;
     if (idx >= nout) break;
-    int r = idx / ns, k = idx - r * ns;
+    const int r = idx / ns, k = idx - r * ns;
     cout[((size_t)r * bg.nblk + blk) * ns + k] = make_float2(acc[o].re, acc[o].im);
   }
 }
