@@ -38,3 +38,16 @@ def test_roofline_record():
     prof["sap_f32"]["flops"] = 1e12        # below the ridge: HBM-bound
     r = bench.roofline(prof, 3000.0, None, pk, sms=152)
     assert r["bound"] == "hbm" and abs(r["achieved"] - 2000.0) < 1e-6
+
+
+def test_iteration_counts_record_and_cpu_sample():
+    """The committed iteration counts (written by oracle/gcr_iteration_counts.py)
+    carry what the CPU baseline needs, and a one-iteration sample of it runs."""
+    import os
+    counts = json.load(open(os.path.join(bench.ROOT, "oracle", "gcr_iteration_counts.json")))
+    for key in ("dims", "eps", "csw", "kappa", "seed", "iters_sloppy", "iters_exact_from_sloppy"):
+        assert key in counts
+    assert counts["residual_sloppy"] <= counts["sloppy_tol"] and counts["residual_exact"] <= counts["exact_tol"]
+    v, desc, cores, v1 = bench.oracle_sample(max_iter=1, parallel=False)
+    assert v > 0 and v1 > 0 and cores == 1
+    assert bench.lattice_label(counts["dims"]) in desc
