@@ -192,11 +192,6 @@ __global__ void __launch_bounds__(128) k_dfl_ypart(const char* __restrict__ phi,
 constexpr int TS = 8;
 constexpr int GEMM_TPB = 256;
 
-__device__ inline Cplx<float> ld_comp(const char* field, int V, int s, int comp) {
-  float4 v = __ldg((const float4*)field + (size_t)(comp >> 1) * V + s);
-  return (comp & 1) ? cmk(v.z, v.w) : cmk(v.x, v.y);
-}
-
 // Projection c[r][b][k] = (phi_k^b, rho_r) for the unmasked right-hand sides.
 // One CTA per block, tiles of TS sites: staging tasks of one field (phi_k or
 // rho_r) at one site, six 16-byte loads for its 12 components, stored entry-
@@ -614,8 +609,8 @@ static int little_threads(int ns, int n) {
 // m steps of block-Jacobi preconditioned GCR on the little vectors from x = 0:
 // res holds the right-hand side on entry and the residual on exit, xl the
 // approximate solution; P, Q: m (p, q) pairs of vlen float2 each.
-static void little_gcr(qcd_ctx* c, DflState* d, float2* res, float2* xl, float2* P, float2* Q, double2* part,
-                       double2* dots, int n, int m, const int* mask) {
+static qcd_status little_gcr(qcd_ctx* c, DflState* d, float2* res, float2* xl, float2* P, float2* Q, double2* part,
+                             double2* dots, int n, int m, const int* mask) {
   const BlkGeom& bg = d->bg;
   const int ns = d->ns;
   const int N = bg.nblk * ns;
@@ -625,7 +620,7 @@ static void little_gcr(qcd_ctx* c, DflState* d, float2* res, float2* xl, float2*
   // dot chunks of about 8 elements per thread (at most G)
   const int Gd = (N + 2047) / 2048 < G ? (N + 2047) / 2048 : G;
   const int nt = little_threads(ns, n);
-  cudaMemsetAsync(xl, 0, sizeof(float2) * vlen, c->stream);
+  QCD_CUDA_OK(cudaMemsetAsync(xl, 0, sizeof(float2) * vlen, c->stream));
   for (int i = 0; i < m; i++) {
     float2* pi = P + vlen * i;
     float2* qi = Q + vlen * i;
@@ -643,6 +638,8 @@ static void little_gcr(qcd_ctx* c, DflState* d, float2* res, float2* xl, float2*
     k_little_sum<<<dim3(1, n), 256, 0, c->stream>>>(part, 1, Gd, dots, n, mask);
     k_little_update<<<gv, 256, 0, c->stream>>>(xl, res, pi, qi, dots, N, mask);
   }
+  QCD_CUDA_OK(cudaGetLastError());
+  return QCD_OK;
 }
 
 static qcd_status dfl_gs(qcd_ctx* c) {
@@ -750,8 +747,7 @@ qcd_status dfl_low_mode(qcd_ctx* c, const void* rho, void* x, int n, const int* 
   {
     ProfScope ps(c, FAM_DFL, 8.0 * vlen * (6.0 + 3.0 * m) * m, 0.0, 4 + 8 * m);
     QCD_CUDA_OK(cudaMemcpyAsync(res, cl, sizeof(float2) * vlen, cudaMemcpyDeviceToDevice, c->stream));
-    little_gcr(c, d, res, xl, P, Q, part, dots, n, m, mask);
-    QCD_CUDA_OK(cudaGetLastError());
+    QCD_TRY(little_gcr(c, d, res, xl, P, Q, part, dots, n, m, mask));
   }
   {
     ProfScope ps(c, FAM_DFL, (double)spinor_bytes(c, QCD_PREC_F32) * (ns + nactive), 8.0 * c->g.V * 12 * ns * nactive);
@@ -790,7 +786,7 @@ qcd_status dfl_little_host(qcd_ctx* c, const double* in, double* out, int n, int
     double2* part = (double2*)d->part.p;
     double2* dots = part + (size_t)n * (m + 2) * G;
     QCD_CUDA_OK(cudaMemcpyAsync(res, x, sizeof(float2) * vlen, cudaMemcpyDeviceToDevice, c->stream));
-    little_gcr(c, d, res, xl, P, Q, part, dots, n, m, nullptr);
+    QCD_TRY(little_gcr(c, d, res, xl, P, Q, part, dots, n, m, nullptr));
     QCD_CUDA_OK(cudaMemcpyAsync(y, xl, sizeof(float2) * vlen, cudaMemcpyDeviceToDevice, c->stream));
   }
   QCD_CUDA_OK(cudaGetLastError());
