@@ -389,10 +389,11 @@ qcd_status qcd_nucleon_2pt_noalloc(const int dims[4], int time_bc, const double*
  * the inverse iteration phi -> M_SAP phi followed by block Gram-Schmidt; then
  * the little Dirac operator A = (phi_k^b, D phi_l^b') (eq. little) on the
  * block and its 8 neighbours (tensor-core GEMMs, FP32-accurate products,
- * FP64 sums and storage), and the FP64 Gauss-Jordan inverses of its
- * diagonal blocks.  QCD_ERR_TIMEOUT if the tensor-core build gave up waiting
- * for its matrix multiplies (a bounded wait; nothing is left running).  1 <= ns <= 32; SAP block extents >= 2 in every
- * direction.  Setting new parameters with a different block size discards
+ * compensated sums, FP64 storage), and the FP64 Gauss-Jordan inverses of its
+ * diagonal blocks; FP32 copies of both serve the little solve of the
+ * deflated preconditioner.  QCD_ERR_TIMEOUT if the tensor-core build gave up
+ * waiting for its matrix multiplies (a bounded wait; nothing is left
+ * running).  1 <= ns <= 32; SAP block extents >= 2 in every direction.  Setting new parameters with a different block size discards
  * the subspace.  Returns QCD_ERR_BREAKDOWN if a diagonal block is singular. */
 qcd_status qcd_deflation_setup(qcd_ctx* ctx, const double* init, int ns, int n_inv);
 /* The deflation fields as ns canonical FP64 spinors (device). */
@@ -402,9 +403,10 @@ qcd_status qcd_deflation_fields(qcd_ctx* ctx, double* out);
  * couples a block to itself, 1 + 2 mu to its neighbour at +mu, 2 + 2 mu to
  * the one at -mu; blocks are numbered ((bt*nbz + bz)*nby + by)*nbx + bx. */
 qcd_status qcd_deflation_little_matrix(qcd_ctx* ctx, double* out);
-/* Little vectors (host FP64 complex [n][block][ns]): mode 0: out = A in;
- * mode 1: out = the m-step block-Jacobi preconditioned GCR approximation of
- * A^-1 in used by the preconditioner. */
+/* Little vectors (host FP64 complex [n][block][ns], rounded to FP32 on the
+ * device): mode 0: out = A in with the FP64 A (FP64 sums); mode 1: out = the
+ * m-step block-Jacobi preconditioned GCR approximation of A^-1 in that the
+ * preconditioner uses (FP32 copies of A and the block inverses). */
 qcd_status qcd_deflation_little(qcd_ctx* ctx, const double* in, double* out, int n, int mode, int m);
 
 /* Kernel timing (no counterpart in the paper; measurement support).  While
