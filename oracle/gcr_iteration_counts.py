@@ -14,8 +14,12 @@ oracle GCR iteration measured on that field and scaled by volume.  (The count
 of an unpreconditioned solver grows with the volume as the lowest modes move
 down, so counts taken on the smaller lattice understate the full-size cost:
 the CPU figure is favourable to the CPU.)  The committed file was written
-with --dims 16 8 8 8: on 16^3x32 the exact solve had not finished after
-several hours on the build machine's cores.
+with --dims 16 8 8 8.  On larger copies the unpreconditioned restarted GCR
+stagnates: with --dims 24 12 12 12 it stopped at its 20,000-iteration cap
+with relative residuals of 3.7e-3 (aiming at 1e-3) and then 1.6e-3 (aiming
+at 1e-10), after 4.9 hours on the build machine's cores; so the counts of the
+smaller field understate the oracle's cost at the benchmark's sizes by a
+large factor.
 
     python -m oracle.gcr_iteration_counts        # writes oracle/gcr_iteration_counts.json
     python -m oracle.gcr_iteration_counts --dims 24 12 12 12 --out <path>   # a smaller copy
